@@ -1,0 +1,71 @@
+"""The synthetic workloads, as recipes (sizes, geometry, point-cloud statistics, seeds).
+
+Each recipe stands in for one of the paper's workloads: seeded random point
+clouds inside the square pyramid of the full field of view, holograms made by
+the point-source model of Eq. 3, at the sizes and fields of view the paper
+reports (up to 16K and 120 degrees).  The Neptune point clouds of Section 5
+are not available; these recipes take their shape (dense random points,
+random phase, wide and ultra-wide FoV) instead.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import points, hologram, tan_half_fov
+
+LAMBDA_532 = 532e-9
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n: int                       # hologram is n x n complex64
+    wavelength: float
+    pitch: float
+    n_points: int
+    z_range: tuple               # point depths, metres
+    amp_range: tuple
+    z_view: float                # reconstruction distance of the full view
+    seed: int
+    spread: float = 1.0          # points lie within spread * full-view half width
+    partial_views: int = 0       # number of seeded partial views
+    partial_size: int = 0        # their size in full-view pixels
+
+    @property
+    def tan_half(self) -> float:
+        return tan_half_fov(self.wavelength, self.pitch)
+
+    def point_cloud(self) -> np.ndarray:
+        return points(self.seed, self.n_points, self.z_range, self.tan_half, self.amp_range,
+                      self.spread)
+
+    def make_hologram(self, threads: int = 0) -> np.ndarray:
+        return hologram(self.point_cloud(), self.wavelength, self.pitch, self.n, self.n, threads)
+
+    def partial_view_offsets(self) -> np.ndarray:
+        """Seeded view centres as integer full-view pixel offsets from the centre.
+
+        Views of partial_size^2 pixels at the full-view pitch, entirely inside
+        the full view.  Returns (partial_views, 2) int64 offsets (dx, dy) of the
+        view centre pixel from the full-view centre pixel.
+        """
+        rng = np.random.default_rng(self.seed + 7)
+        lim = (self.n - self.partial_size) // 2
+        return rng.integers(-lim, lim + 1, size=(self.partial_views, 2)).astype(np.int64)
+
+
+# Full-view reconstruction of a small CGH (8 points, unit amplitude).
+SMALL_512 = Workload("pointcloud-512-532nm-0.4um-8pt", 512, LAMBDA_532, 0.4e-6, 8,
+                     (0.5e-3, 2.0e-3), (1.0, 1.0), 1.0e-3, seed=20241017)
+# Wide-angle 4096^2, 2000 points in a frustum z in [1, 5] mm, full view at 3 mm.
+WA_4096 = Workload("pointcloud-4096-532nm-0.5um-2000pt", 4096, LAMBDA_532, 0.5e-6, 2000,
+                   (1.0e-3, 5.0e-3), (0.5, 1.0), 3.0e-3, seed=20241018)
+# Ultra-wide-angle 16384^2 (120 deg), 20000 points in z in [2, 10] mm,
+# full view at 6 mm plus 16 partial views of 2048^2 at the full-view pitch.
+UWA_16K = Workload("pointcloud-16384-532nm-0.307um-20000pt", 16384, LAMBDA_532, 0.307e-6,
+                   20000, (2.0e-3, 10.0e-3), (0.5, 1.0), 6.0e-3, seed=20241019,
+                   partial_views=16, partial_size=2048)
+
+ALL = {w.name: w for w in (SMALL_512, WA_4096, UWA_16K)}
