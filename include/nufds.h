@@ -1,0 +1,161 @@
+/*
+ * nufds.h -- C ABI of the GB300 NU-FDS reconstruction library (libnufds.so).
+ *
+ * NU-FDS (Kozacki et al., "Non-uniform Fourier Domain Stretching method for
+ * ultra-wide-angle wave propagation") reconstructs the object field of a
+ * wide-angle computer-generated hologram at distance z:
+ *   step two (Section 4, Fig. 3): FT of the hologram, the non-uniform
+ *     frequency stretch f' = (f_x m_x, f_y m_y) of Eqs. 9, 10 with the
+ *     magnification of Eq. 16, resampling onto a uniform f' grid, inverse FT;
+ *   step three: the Fresnel transform of Eq. 2 (chirp, FT, chirp);
+ *   step five: the output remap O(x_o) = O'(x_o') with x_o' from Eqs. 17-18,
+ *     sampled on a uniform grid of the requested (full or partial) view.
+ * Problem statement followed by the parameters: wavelength, pixel pitch,
+ * N_x x N_y hologram (Section 2), distance z_o, output window and sampling
+ * (Section 4, output-grid choice; partial view: Section 4, last part).
+ *
+ * Conventions.  Hologram sample (ix, iy) sits at x = (ix - N_x/2) pitch,
+ * y = (iy - N_y/2) pitch.  Output pixel (i, j) of a view sits at
+ * x_o = center_x + (i - out_nx/2) * width/out_nx (same for y).  Transform
+ * kernel e^{-2 pi i x f}; chirps e^{+i pi r^2/(lambda z)}; no 1/(i lambda z)
+ * factor (Eq. 2 has none); forward DFT unnormalised, inverse DFT scaled by
+ * 1/N'^2.  A unit point source focused at the view centre gives |O|^2 ~ N^4.
+ *
+ * Buffers.  Every pointer called d_* is a DEVICE pointer owned by the caller.
+ * Holograms are row-major interleaved complex64 (8 bytes per sample, 8-byte
+ * aligned), N_y rows of N_x samples.  Outputs are row-major out_ny x out_nx,
+ * float32 intensity |O|^2 (4 bytes per pixel) or interleaved complex64 field
+ * (8 bytes per pixel).  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream).  Calls are asynchronous on that stream unless stated.
+ *
+ * Errors.  Every int-returning call returns NUFDS_OK (0) or a negative code;
+ * nufds_status_string() names it.  No C++ exception crosses the ABI.  A plan
+ * is used by one host thread at a time; different plans are independent.
+ */
+#ifndef NUFDS_H
+#define NUFDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NUFDS_OK 0
+#define NUFDS_EINVAL (-1)       /* bad argument: lambda >= 2 pitch, z <= 0, sizes, NULL */
+#define NUFDS_ENOMEM (-2)       /* HBM budget exceeded or cudaMalloc failed             */
+#define NUFDS_EUNSUPPORTED (-3) /* valid but not supported (size limits, view outside FoV) */
+#define NUFDS_ECUDA (-4)        /* a CUDA runtime call failed                            */
+#define NUFDS_ETIMEOUT (-5)     /* a bounded device-side wait gave up                    */
+
+/* storage of the cached spectrum and of the inter-pass arrays (arithmetic is FP32) */
+#define NUFDS_FP32 0
+#define NUFDS_FP16_STORE 1
+#define NUFDS_BF16_STORE 2
+
+#define NUFDS_OUT_INTENSITY_F32 0
+#define NUFDS_OUT_FIELD_C64 1
+
+typedef struct nufds_plan nufds_plan;
+
+typedef struct nufds_params {
+    double wavelength_m;       /* lambda > 0, lambda < 2 pitch (Eq. 1)                  */
+    double pitch_m;            /* hologram pixel pitch Delta                            */
+    int32_t nx, ny;            /* hologram size; each a multiple of 4, 16 <= n <= 16384 */
+    int32_t precision;         /* NUFDS_FP32 (only value supported so far)              */
+    int32_t reserved;          /* must be 0                                             */
+    uint64_t hbm_budget_bytes; /* cap on device memory the plan may allocate; 0 = none  */
+} nufds_params;
+
+typedef struct nufds_view {
+    double z_m;                /* reconstruction distance z_o > 0                       */
+    double center_x_m;         /* view centre in the object plane                       */
+    double center_y_m;
+    double width_m;            /* view size; 0,0 = full view B = 2 z tan(asin(l/2D))    */
+    double height_m;
+    int32_t out_nx, out_ny;    /* output pixels; 0,0 = N_x, N_y                         */
+    int32_t out_kind;          /* NUFDS_OUT_INTENSITY_F32 or NUFDS_OUT_FIELD_C64        */
+    int32_t reserved;          /* must be 0                                             */
+} nufds_view;
+
+/* What the planner decided for one view (Section 4 output grid; band from Eq. 17). */
+typedef struct nufds_view_info {
+    int64_t out_nx, out_ny;
+    int64_t k_lo_x, k_hi_x, k_lo_y, k_hi_y; /* stretched-spectrum band, lattice 1/(N pitch) */
+    int64_t np_x, np_y;                     /* FFT size N' of the band per axis             */
+    int64_t k_c_x, k_c_y;                   /* band centre, at index N'/2                   */
+    double pitch_out_x_m, pitch_out_y_m;
+    double width_m, height_m;
+    int32_t on_full_view_lattice;           /* 1: pixels are a window of the full view's   */
+    int32_t reserved;
+    uint64_t workspace_bytes;               /* device workspace this view needs             */
+} nufds_view_info;
+
+/*
+ * Create a plan for one hologram geometry and (optionally) load a hologram.
+ * Builds, on the device and once per plan, the FP64-derived tables of the
+ * inverse stretch (Eqs. 9, 10, 16) on the full-view band and of the output
+ * map (Eq. 17) on the full-view pixel lattice; then, if d_hologram_c64 is not
+ * NULL, computes and caches its oversampled spectrum (step two, "FT of the
+ * hologram").  Synchronises cuda_stream before returning; the caller may free
+ * the hologram afterwards.  *out receives the plan (NULL on error).
+ */
+int nufds_plan_create(const nufds_params *params, const void *d_hologram_c64,
+                      void *cuda_stream, nufds_plan **out);
+
+/*
+ * Replace the plan's hologram (same geometry): recompute the cached
+ * oversampled spectrum from d_hologram_c64.  Asynchronous on cuda_stream;
+ * the hologram must stay valid until the stream reaches this point.
+ */
+int nufds_plan_load(nufds_plan *plan, const void *d_hologram_c64, void *cuda_stream);
+
+/*
+ * Plan one view for a hologram geometry without touching the GPU (host FP64
+ * only; fills *info).  Band: floor/ceil of the Eq. 17 image, in stretched-
+ * lattice units N pitch f', of every boundary pixel centre of the view; FFT
+ * size N' = nice(max(band width, ceil((N pitch)^2/(lambda z)))) with nice(n)
+ * the smallest 2^a 3^b 5^c >= n, a >= 6, b <= 2, c <= 1.
+ */
+int nufds_view_plan(const nufds_params *params, const nufds_view *view, nufds_view_info *info);
+
+/*
+ * Reconstruct one view of the loaded hologram into d_out (out_ny x out_nx,
+ * float32 intensity or complex64 field).  Asynchronous on cuda_stream.  The
+ * plan's workspace grows on first use of a larger view (that call allocates
+ * and synchronises).  Views whose band leaves the full-view band are
+ * NUFDS_EUNSUPPORTED.
+ */
+int nufds_reconstruct(nufds_plan *plan, const nufds_view *view, void *d_out, void *cuda_stream);
+
+/*
+ * Reconstruct count views, each of its own plan, in order on cuda_stream.
+ * statuses (may be NULL) receives one code per view; a failing view does not
+ * stop the others.  Returns NUFDS_OK if every view succeeded, else the first
+ * error code.
+ */
+int nufds_reconstruct_batch(nufds_plan *const *plans, const nufds_view *views,
+                            void *const *d_outs, int32_t count, void *cuda_stream,
+                            int32_t *statuses);
+
+/* Free the plan and its device memory (synchronises its streams).  NULL-safe. */
+void nufds_destroy(nufds_plan *plan);
+
+/* Bytes of device memory the plan holds. */
+uint64_t nufds_plan_device_bytes(const nufds_plan *plan);
+
+/* Static name of a status code. */
+const char *nufds_status_string(int status);
+
+/*
+ * Number of kernel launches issued by this library on the calling thread
+ * since the last reset (reset = 1 zeroes it after reading).  Lets a caller
+ * count the GPU work a call made.
+ */
+int64_t nufds_launch_count(int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUFDS_H */

@@ -1,0 +1,216 @@
+"""GB300 NU-FDS reconstruction of wide-angle holograms: thin Python binding.
+
+The work runs in libnufds.so (hand-written sm_103a CUDA behind the C ABI of
+include/nufds.h).  This module only marshals arguments: torch provides device
+memory and streams.  There is no CPU fallback: if the library is not built,
+``lib()`` raises.
+
+    import torch, paper_2410_13474_gb300 as nf
+    plan = nf.Plan(wavelength=532e-9, pitch=0.4e-6, nx=512, ny=512, hologram=h)  # h: cuda complex64
+    out = plan.reconstruct(nf.View(z=1e-3))                                     # float32 intensity
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnufds.so")
+
+OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
+FP32, FP16_STORE, BF16_STORE = 0, 1, 2
+OUT_INTENSITY, OUT_FIELD = 0, 1
+
+# every function include/nufds.h declares
+ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",
+                 "nufds_reconstruct_batch", "nufds_destroy", "nufds_plan_device_bytes",
+                 "nufds_status_string", "nufds_launch_count")
+
+
+class NufdsError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, status_string(code), code))
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("wavelength_m", ctypes.c_double), ("pitch_m", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class _View(ctypes.Structure):
+    _fields_ = [("z_m", ctypes.c_double), ("center_x_m", ctypes.c_double),
+                ("center_y_m", ctypes.c_double), ("width_m", ctypes.c_double),
+                ("height_m", ctypes.c_double), ("out_nx", ctypes.c_int32),
+                ("out_ny", ctypes.c_int32), ("out_kind", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class _ViewInfo(ctypes.Structure):
+    _fields_ = [("out_nx", ctypes.c_int64), ("out_ny", ctypes.c_int64),
+                ("k_lo_x", ctypes.c_int64), ("k_hi_x", ctypes.c_int64),
+                ("k_lo_y", ctypes.c_int64), ("k_hi_y", ctypes.c_int64),
+                ("np_x", ctypes.c_int64), ("np_y", ctypes.c_int64),
+                ("k_c_x", ctypes.c_int64), ("k_c_y", ctypes.c_int64),
+                ("pitch_out_x_m", ctypes.c_double), ("pitch_out_y_m", ctypes.c_double),
+                ("width_m", ctypes.c_double), ("height_m", ctypes.c_double),
+                ("on_full_view_lattice", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libnufds.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnufds.so is not built (run paper_2410_13474_gb300.build.build());"
+                               " there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.nufds_plan_create.argtypes = [ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(vp)]
+        L.nufds_plan_load.argtypes = [vp, vp, vp]
+        L.nufds_view_plan.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_View),
+                                      ctypes.POINTER(_ViewInfo)]
+        L.nufds_reconstruct.argtypes = [vp, ctypes.POINTER(_View), vp, vp]
+        L.nufds_reconstruct_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_View),
+                                              ctypes.POINTER(vp), ctypes.c_int32, vp,
+                                              ctypes.POINTER(ctypes.c_int32)]
+        L.nufds_destroy.argtypes = [vp]
+        L.nufds_destroy.restype = None
+        L.nufds_plan_device_bytes.argtypes = [vp]
+        L.nufds_plan_device_bytes.restype = ctypes.c_uint64
+        L.nufds_status_string.argtypes = [ctypes.c_int]
+        L.nufds_status_string.restype = ctypes.c_char_p
+        L.nufds_launch_count.argtypes = [ctypes.c_int32]
+        L.nufds_launch_count.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().nufds_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise NufdsError(code, what)
+
+
+def launch_count(reset: bool = False) -> int:
+    """Kernel launches this library issued on the calling thread (see nufds_launch_count)."""
+    return int(lib().nufds_launch_count(1 if reset else 0))
+
+
+@dataclass
+class View:
+    """One requested view: distance z, centre and size in the object plane
+    (0,0 = full view of Eq. 1), output pixels (0,0 = hologram size)."""
+    z: float
+    center_x: float = 0.0
+    center_y: float = 0.0
+    width: float = 0.0
+    height: float = 0.0
+    out_nx: int = 0
+    out_ny: int = 0
+    kind: int = OUT_INTENSITY
+
+    def _c(self) -> _View:
+        return _View(self.z, self.center_x, self.center_y, self.width, self.height,
+                     self.out_nx, self.out_ny, self.kind, 0)
+
+
+def _params(wavelength, pitch, nx, ny, precision=FP32, budget=0) -> _Params:
+    return _Params(wavelength, pitch, nx, ny, precision, 0, budget)
+
+
+def view_plan(wavelength: float, pitch: float, nx: int, ny: int, view: View) -> dict:
+    """Host-only planner result for one view (band, FFT sizes N', output grid)."""
+    info = _ViewInfo()
+    p = _params(wavelength, pitch, nx, ny)
+    v = view._c()
+    _check(lib().nufds_view_plan(ctypes.byref(p), ctypes.byref(v), ctypes.byref(info)),
+           "nufds_view_plan")
+    return {name: getattr(info, name) for name, _ in _ViewInfo._fields_ if name != "reserved"}
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A hologram geometry with its FP64-derived tables and (once loaded) the
+    cached oversampled spectrum of one hologram, on the current CUDA device."""
+
+    def __init__(self, wavelength: float, pitch: float, nx: int, ny: int, hologram=None,
+                 stream=None, precision: int = FP32, budget: int = 0):
+        self.wavelength, self.pitch, self.nx, self.ny = wavelength, pitch, nx, ny
+        self._p = ctypes.c_void_p()
+        prm = _params(wavelength, pitch, nx, ny, precision, budget)
+        holo = None if hologram is None else self._holo_ptr(hologram)
+        _check(lib().nufds_plan_create(ctypes.byref(prm), holo, _stream_handle(stream),
+                                       ctypes.byref(self._p)), "nufds_plan_create")
+
+    def _holo_ptr(self, h):
+        import torch
+        if not (h.is_cuda and h.dtype == torch.complex64 and h.is_contiguous()
+                and tuple(h.shape) == (self.ny, self.nx)):
+            raise ValueError("hologram must be a contiguous cuda complex64 tensor of shape (ny, nx)")
+        return ctypes.c_void_p(h.data_ptr())
+
+    def load(self, hologram, stream=None):
+        _check(lib().nufds_plan_load(self._p, self._holo_ptr(hologram), _stream_handle(stream)),
+               "nufds_plan_load")
+
+    def view_plan(self, view: View) -> dict:
+        return view_plan(self.wavelength, self.pitch, self.nx, self.ny, view)
+
+    def output_like(self, view: View):
+        import torch
+        info = self.view_plan(view)
+        dt = torch.float32 if view.kind == OUT_INTENSITY else torch.complex64
+        return torch.empty((info["out_ny"], info["out_nx"]), dtype=dt, device="cuda")
+
+    def reconstruct(self, view: View, out=None, stream=None):
+        import torch
+        if out is None:
+            out = self.output_like(view)
+        want = torch.float32 if view.kind == OUT_INTENSITY else torch.complex64
+        if not (out.is_cuda and out.dtype == want and out.is_contiguous()):
+            raise ValueError("out must be a contiguous cuda %s tensor" % want)
+        v = view._c()
+        _check(lib().nufds_reconstruct(self._p, ctypes.byref(v), ctypes.c_void_p(out.data_ptr()),
+                                       _stream_handle(stream)), "nufds_reconstruct")
+        return out
+
+    def device_bytes(self) -> int:
+        return int(lib().nufds_plan_device_bytes(self._p))
+
+    def close(self):
+        if self._p:
+            lib().nufds_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reconstruct_batch(plans, views, outs, stream=None):
+    """Reconstruct views[i] of plans[i] into outs[i] in order; returns per-view status codes."""
+    n = len(views)
+    pa = (ctypes.c_void_p * n)(*[p._p.value for p in plans])
+    va = (_View * n)(*[v._c() for v in views])
+    oa = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    st = (ctypes.c_int32 * n)()
+    lib().nufds_reconstruct_batch(pa, va, oa, n, _stream_handle(stream), st)
+    return list(st)

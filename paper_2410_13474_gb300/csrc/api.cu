@@ -1,0 +1,553 @@
+// C ABI of libnufds: plans, the view planner, workspace and the launch sequence.
+//
+// Launch sequence of one view (Section 4, Fig. 3, steps two, three and five):
+//   stretch     S_T[jx][jy] = H~(f(f'_k)) (-1)^(jx+jy)       gather from G (cached)
+//   rows_view   along y: inverse DFT, chirp_y, 2x-oversampled forward DFT
+//   transpose
+//   rows_view   along x: the same -> Q, the oversampled Fresnel transform
+//   remap       O(x_o) = Q at x'(x_o) (Eq. 17), |O|^2 or O * chirp_out
+// Hologram load (step two, "FT of the hologram"):
+//   rows_pad2 along x, transpose, rows_pad2 along y -> G[mx][my]
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <list>
+#include <mutex>
+#include <new>
+
+#include "../../include/nufds.h"
+#include "internal.cuh"
+
+namespace nufds {
+
+static thread_local int64_t t_launches = 0;
+void count_launch() { ++t_launches; }
+int check_launch() { return cudaPeekAtLastError() == cudaSuccess ? 0 : NUFDS_ECUDA; }
+
+struct ViewPlan {
+    int ox, oy;
+    long klo_x, khi_x, klo_y, khi_y, kc_x, kc_y;
+    int npx, npy;
+    double px, py, w, h, z, cx, cy;
+    bool lattice;
+    long i0, j0;
+};
+
+struct ViewKey {
+    double z, cx, cy, w, h;
+    int ox, oy;
+    bool operator==(const ViewKey &o) const { return memcmp(this, &o, sizeof(ViewKey)) == 0; }
+};
+
+}  // namespace nufds
+
+using namespace nufds;
+
+struct nufds_plan {
+    int device = 0;
+    double lam = 0, pitch = 0;
+    int nx = 0, ny = 0;
+    uint64_t budget = 0;
+    const FftPlan *fx = nullptr, *fy = nullptr;
+    // full-view band (z independent in lattice units) and its pull-back table
+    long pb_kx0 = 0, pb_ky0 = 0;
+    int pb_nkx = 0, pb_nky = 0;
+    short2 *pb_base = nullptr;
+    float2 *pb_frac = nullptr;
+    // output map on the full-view pixel lattice (z independent)
+    short2 *rm_base = nullptr;
+    float2 *rm_frac = nullptr;
+    // cached oversampled spectrum, [mx][my]
+    float2 *G = nullptr;
+    bool loaded = false;
+    // workspace arena
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t fixed_bytes = 0;
+    std::list<std::pair<ViewKey, ViewPlan>> vcache;
+};
+
+namespace nufds {
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static double full_width(double lam, double pitch, double z) {
+    double st = lam / (2.0 * pitch);
+    return 2.0 * z * st / sqrt(1.0 - st * st);  // Eq. 1
+}
+
+// smallest 2^a 3^b 5^c >= n with a >= 6, b <= 2, c <= 1
+static long nice_size(long n) {
+    long best = -1;
+    const long bases[6] = {1, 3, 9, 5, 15, 45};
+    for (long b : bases) {
+        long v = 64 * b;
+        while (v < n) v *= 2;
+        if (best < 0 || v < best) best = v;
+    }
+    return best;
+}
+
+// The planner: band = floor/ceil of the Eq. 17 image of all boundary pixel
+// centres in lattice units N pitch f'; N' = nice(max(band, (N pitch)^2/(lambda z))).
+struct Geom {
+    double lam, pitch;
+    int nx, ny;
+};
+
+static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
+    if (!v || !(v->z_m > 0) || v->reserved != 0) return NUFDS_EINVAL;
+    if (v->out_kind != NUFDS_OUT_INTENSITY_F32 && v->out_kind != NUFDS_OUT_FIELD_C64)
+        return NUFDS_EINVAL;
+    const double lam = P->lam, pitch = P->pitch, z = v->z_m;
+    double w = v->width_m, h = v->height_m;
+    const double B = full_width(lam, pitch, z);
+    if (w <= 0 || h <= 0) {
+        if (w != 0 || h != 0) return NUFDS_EINVAL;
+        w = B;
+        h = B;
+    }
+    int ox = v->out_nx, oy = v->out_ny;
+    if (ox <= 0 || oy <= 0) {
+        if (ox != 0 || oy != 0) return NUFDS_EINVAL;
+        ox = P->nx;
+        oy = P->ny;
+    }
+    if (ox > 65536 || oy > 65536) return NUFDS_EUNSUPPORTED;
+    o->ox = ox;
+    o->oy = oy;
+    o->px = w / ox;
+    o->py = h / oy;
+    o->w = w;
+    o->h = h;
+    o->z = z;
+    o->cx = v->center_x_m;
+    o->cy = v->center_y_m;
+    double kmin[2] = {1e300, 1e300}, kmax[2] = {-1e300, -1e300};
+    const long nb = 2L * ox + 2L * oy;
+    for (long t = 0; t < nb; ++t) {
+        int i, j;
+        if (t < ox) { i = (int)t; j = 0; }
+        else if (t < 2L * ox) { i = (int)(t - ox); j = oy - 1; }
+        else if (t < 2L * ox + oy) { i = 0; j = (int)(t - 2L * ox); }
+        else { i = ox - 1; j = (int)(t - 2L * ox - oy); }
+        double xo = o->cx + (i - 0.5 * ox) * o->px, yo = o->cy + (j - 0.5 * oy) * o->py;
+        double R0 = sqrt(xo * xo + yo * yo + z * z);
+        double up, vp;
+        host_phi(xo / R0, yo / R0, &up, &vp);
+        double kx = P->nx * pitch * up / lam, ky = P->ny * pitch * vp / lam;
+        kmin[0] = fmin(kmin[0], kx);
+        kmax[0] = fmax(kmax[0], kx);
+        kmin[1] = fmin(kmin[1], ky);
+        kmax[1] = fmax(kmax[1], ky);
+    }
+    o->klo_x = (long)floor(kmin[0]);
+    o->khi_x = (long)ceil(kmax[0]);
+    o->klo_y = (long)floor(kmin[1]);
+    o->khi_y = (long)ceil(kmax[1]);
+    double chx = ceil((P->nx * pitch) * (P->nx * pitch) / (lam * z));
+    double chy = ceil((P->ny * pitch) * (P->ny * pitch) / (lam * z));
+    long wx = o->khi_x - o->klo_x + 1, wy = o->khi_y - o->klo_y + 1;
+    long npx = nice_size(wx > (long)chx ? wx : (long)chx);
+    long npy = nice_size(wy > (long)chy ? wy : (long)chy);
+    if (npx > 24576 || npy > 24576) return NUFDS_EUNSUPPORTED;  // one row per CTA in smem
+    o->npx = (int)npx;
+    o->npy = (int)npy;
+    o->kc_x = (long)floor(0.5 * (double)(o->klo_x + o->khi_x));
+    o->kc_y = (long)floor(0.5 * (double)(o->klo_y + o->khi_y));
+    // pixels on the full view's lattice?  (then the plan's output-map table serves)
+    const double fpx = B / P->nx, fpy = B / P->ny;
+    o->lattice = false;
+    if (fabs(o->px - fpx) <= 1e-12 * fpx && fabs(o->py - fpy) <= 1e-12 * fpy) {
+        double ri = o->cx / fpx - 0.5 * ox + 0.5 * P->nx;
+        double rj = o->cy / fpy - 0.5 * oy + 0.5 * P->ny;
+        double ii = rint(ri), jj = rint(rj);
+        if (fabs(ri - ii) < 1e-9 && fabs(rj - jj) < 1e-9 && ii >= 0 && jj >= 0 &&
+            ii + ox <= P->nx && jj + oy <= P->ny) {
+            o->lattice = true;
+            o->i0 = (long)ii;
+            o->j0 = (long)jj;
+        }
+    }
+    return NUFDS_OK;
+}
+
+static int plan_view_cached(nufds_plan *P, const nufds_view *v, ViewPlan *o) {
+    ViewKey key;
+    memset(&key, 0, sizeof key);
+    key.z = v->z_m;
+    key.cx = v->center_x_m;
+    key.cy = v->center_y_m;
+    key.w = v->width_m;
+    key.h = v->height_m;
+    key.ox = v->out_nx;
+    key.oy = v->out_ny;
+    for (auto it = P->vcache.begin(); it != P->vcache.end(); ++it)
+        if (it->first == key) {
+            *o = it->second;
+            P->vcache.splice(P->vcache.begin(), P->vcache, it);
+            return v->out_kind == NUFDS_OUT_INTENSITY_F32 || v->out_kind == NUFDS_OUT_FIELD_C64
+                       ? NUFDS_OK
+                       : NUFDS_EINVAL;
+        }
+    Geom g = {P->lam, P->pitch, P->nx, P->ny};
+    int rc = plan_view_impl(&g, v, o);
+    if (rc) return rc;
+    P->vcache.emplace_front(key, *o);
+    if (P->vcache.size() > 64) P->vcache.pop_back();
+    return NUFDS_OK;
+}
+
+// Workspace layout of one view (bytes): A (Q and the first pass output),
+// B (S and the transposed pass input), scratch of the view passes, tables.
+struct ViewWs {
+    size_t A, B, scr, chirp, outc, rm, total;
+    int grid_y, grid_x;
+    long ex_b0, ey_b0;
+    int nbx, nby;
+};
+
+static int view_ws(const nufds_plan *P, const ViewPlan &V, const FftPlan *fpx, const FftPlan *fpy,
+                   int kind, ViewWs *w) {
+    const size_t np = (size_t)V.npx * V.npy;
+    w->A = align256(sizeof(float2) * 4 * np);
+    w->B = align256(sizeof(float2) * 2 * np);
+    w->grid_y = rows_view_grid(*fpy, V.npx);
+    w->grid_x = rows_view_grid(*fpx, 2 * V.npy);
+    size_t sy = (size_t)w->grid_y * V.npy, sx = (size_t)w->grid_x * V.npx;
+    w->scr = align256(sizeof(float2) * (sy > sx ? sy : sx));
+    w->chirp = align256(sizeof(float2) * (V.npx + V.npy));
+    w->ex_b0 = 2 * V.klo_x - 8;
+    w->ey_b0 = 2 * V.klo_y - 8;
+    w->nbx = (int)(2 * (V.khi_x - V.klo_x) + 17);
+    w->nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
+    w->outc = kind == NUFDS_OUT_FIELD_C64 ? align256(sizeof(float2) * (w->nbx + w->nby)) : 0;
+    w->rm = V.lattice ? 0 : align256((sizeof(short2) + sizeof(float2)) * (size_t)V.ox * V.oy + 256);
+    w->total = w->A + w->B + w->scr + w->chirp + w->outc + w->rm;
+    (void)P;
+    return NUFDS_OK;
+}
+
+static int ensure_ws(nufds_plan *P, size_t need) {
+    if (need <= P->ws_bytes) return NUFDS_OK;
+    if (P->budget && P->fixed_bytes + need > P->budget) return NUFDS_ENOMEM;
+    if (P->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(P->ws);
+        P->ws = nullptr;
+        P->ws_bytes = 0;
+    }
+    if (cudaMalloc(&P->ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return NUFDS_ENOMEM;
+    }
+    P->ws_bytes = need;
+    return NUFDS_OK;
+}
+
+static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
+    const size_t half = align256(sizeof(float2) * 2 * (size_t)P->nx * P->ny);
+    int rc = ensure_ws(P, 2 * half);
+    if (rc) return rc;
+    float2 *A = (float2 *)P->ws, *Bf = (float2 *)(P->ws + half);
+    const float2 *H = (const float2 *)d_holo;
+    // along x: rows of H (ny rows of nx) -> A (ny x 2nx)
+    if ((rc = launch_rows_pad2(*P->fx, H, P->nx, A, 2 * P->nx, P->ny, st))) return rc;
+    // A (ny x 2nx) -> Bf (2nx x ny)
+    if ((rc = launch_transpose(A, 2 * P->nx, Bf, P->ny, P->ny, 2 * P->nx, st))) return rc;
+    // along y: rows of Bf (2nx rows of ny) -> G (2nx x 2ny)
+    if ((rc = launch_rows_pad2(*P->fy, Bf, P->ny, P->G, 2 * P->ny, 2 * P->nx, st))) return rc;
+    P->loaded = true;
+    return NUFDS_OK;
+}
+
+static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cudaStream_t st) {
+    if (!P || !v || !d_out) return NUFDS_EINVAL;
+    if (!P->loaded) return NUFDS_EINVAL;
+    int rc;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return NUFDS_EINVAL;
+    ViewPlan V;
+    if ((rc = plan_view_cached(P, v, &V))) return rc;
+    if (V.klo_x < P->pb_kx0 || V.khi_x >= P->pb_kx0 + P->pb_nkx || V.klo_y < P->pb_ky0 ||
+        V.khi_y >= P->pb_ky0 + P->pb_nky)
+        return NUFDS_EUNSUPPORTED;
+    const FftPlan *fpx, *fpy;
+    if ((rc = fft_plan_get(V.npx, &fpx))) return rc;
+    if ((rc = fft_plan_get(V.npy, &fpy))) return rc;
+    ViewWs W;
+    view_ws(P, V, fpx, fpy, v->out_kind, &W);
+    if ((rc = ensure_ws(P, W.total))) return rc;
+    char *p = P->ws;
+    float2 *A = (float2 *)p;
+    p += W.A;
+    float2 *Bf = (float2 *)p;
+    p += W.B;
+    float2 *scr = (float2 *)p;
+    p += W.scr;
+    float2 *chx = (float2 *)p, *chy = chx + V.npx;
+    p += W.chirp;
+    float2 *Ex = (float2 *)p, *Ey = Ex + W.nbx;
+    p += W.outc;
+    short2 *rmb = P->rm_base;
+    float2 *rmf = P->rm_frac;
+    long rm_ld = P->nx, rm_i0 = 0, rm_j0 = 0;
+    if (V.lattice) {
+        rm_i0 = V.i0;
+        rm_j0 = V.j0;
+    } else {
+        rmf = (float2 *)p;
+        rmb = (short2 *)(p + align256(sizeof(float2) * (size_t)V.ox * V.oy));
+        rm_ld = V.ox;
+        if ((rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px, V.py,
+                                     V.ox, V.oy, rmb, rmf, st)))
+            return rc;
+    }
+    // chirp tables (FP64 phases), window N pitch, x_n = (n - N'/2) N pitch / N'
+    if ((rc = launch_chirp_table(fpx->deapod, V.npx, P->nx * P->pitch, P->lam, V.z, chx, st)))
+        return rc;
+    if ((rc = launch_chirp_table(fpy->deapod, V.npy, P->ny * P->pitch, P->lam, V.z, chy, st)))
+        return rc;
+    const double kx = M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch));
+    const double ky = M_PI * P->lam * V.z / ((P->ny * P->pitch) * (P->ny * P->pitch));
+    if (v->out_kind == NUFDS_OUT_FIELD_C64) {
+        if ((rc = launch_outchirp_table(kx, W.ex_b0, W.nbx, Ex, st))) return rc;
+        if ((rc = launch_outchirp_table(ky, W.ey_b0, W.nby, Ey, st))) return rc;
+    }
+    // step two: stretch gather -> S_T in Bf (npx x npy)
+    StretchArgs sa;
+    sa.G = P->G;
+    sa.Nx = P->nx;
+    sa.Ny = P->ny;
+    sa.pb_base = P->pb_base;
+    sa.pb_frac = P->pb_frac;
+    sa.pb_kx0 = P->pb_kx0;
+    sa.pb_ky0 = P->pb_ky0;
+    sa.pb_nkx = P->pb_nkx;
+    sa.pb_nky = P->pb_nky;
+    sa.klo_x = V.klo_x;
+    sa.khi_x = V.khi_x;
+    sa.klo_y = V.klo_y;
+    sa.khi_y = V.khi_y;
+    sa.kc_x = V.kc_x;
+    sa.kc_y = V.kc_y;
+    sa.npx = V.npx;
+    sa.npy = V.npy;
+    sa.S = Bf;
+    if ((rc = launch_stretch(sa, st))) return rc;
+    // steps two/three along y: S_T rows (npx of npy) -> A (npx x 2npy)
+    if ((rc = launch_rows_view(*fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y, st)))
+        return rc;
+    // A (npx x 2npy) -> Bf (2npy x npx)
+    if ((rc = launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, st))) return rc;
+    // along x: Bf rows (2npy of npx) -> A = Q (2npy x 2npx)
+    if ((rc = launch_rows_view(*fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr, W.grid_x, st)))
+        return rc;
+    // step five: remap
+    RemapArgs ra;
+    ra.Q = A;
+    ra.npx = V.npx;
+    ra.npy = V.npy;
+    ra.kc_x = V.kc_x;
+    ra.kc_y = V.kc_y;
+    ra.rm_base = rmb;
+    ra.rm_frac = rmf;
+    ra.rm_ld = rm_ld;
+    ra.rm_i0 = rm_i0;
+    ra.rm_j0 = rm_j0;
+    ra.ox = V.ox;
+    ra.oy = V.oy;
+    ra.kind = v->out_kind;
+    ra.Ex = Ex;
+    ra.Ey = Ey;
+    ra.ex_b0 = W.ex_b0;
+    ra.ey_b0 = W.ey_b0;
+    ra.kappa_x = (float)kx;
+    ra.kappa_y = (float)ky;
+    ra.out = d_out;
+    return launch_remap(ra, st);
+}
+
+static void free_plan(nufds_plan *P) {
+    if (!P) return;
+    cudaFree(P->pb_base);
+    cudaFree(P->pb_frac);
+    cudaFree(P->rm_base);
+    cudaFree(P->rm_frac);
+    cudaFree(P->G);
+    cudaFree(P->ws);
+    delete P;
+}
+
+static bool fft_size_ok(int n) {
+    if (n < 16 || n > 16384 || n % 4) return false;
+    int m = n;
+    for (int p : {2, 3, 5})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+}  // namespace nufds
+
+extern "C" {
+
+const char *nufds_status_string(int s) {
+    switch (s) {
+        case NUFDS_OK: return "ok";
+        case NUFDS_EINVAL: return "invalid argument";
+        case NUFDS_ENOMEM: return "out of device memory or HBM budget";
+        case NUFDS_EUNSUPPORTED: return "unsupported";
+        case NUFDS_ECUDA: return "CUDA error";
+        case NUFDS_ETIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int64_t nufds_launch_count(int32_t reset) {
+    int64_t v = t_launches;
+    if (reset) t_launches = 0;
+    return v;
+}
+
+int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream, nufds_plan **out) {
+    if (!out) return NUFDS_EINVAL;
+    *out = nullptr;
+    if (!prm || !(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
+        !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->reserved != 0 || prm->nx <= 0 ||
+        prm->ny <= 0 || prm->nx % 4 || prm->ny % 4)
+        return NUFDS_EINVAL;
+    if (prm->precision != NUFDS_FP32) return NUFDS_EUNSUPPORTED;
+    if (!fft_size_ok(prm->nx) || !fft_size_ok(prm->ny)) return NUFDS_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    nufds_plan *P = new (std::nothrow) nufds_plan();
+    if (!P) return NUFDS_ENOMEM;
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        delete P;
+        return NUFDS_ECUDA;
+    }
+    P->lam = prm->wavelength_m;
+    P->pitch = prm->pitch_m;
+    P->nx = prm->nx;
+    P->ny = prm->ny;
+    P->budget = prm->hbm_budget_bytes;
+    int rc;
+    if ((rc = fft_plan_get(P->nx, &P->fx)) || (rc = fft_plan_get(P->ny, &P->fy))) {
+        free_plan(P);
+        return rc;
+    }
+    // full-view band (z = 1: lattice units do not depend on z)
+    nufds_view fv;
+    memset(&fv, 0, sizeof fv);
+    fv.z_m = 1.0;
+    ViewPlan V;
+    Geom g = {P->lam, P->pitch, P->nx, P->ny};
+    if ((rc = plan_view_impl(&g, &fv, &V))) {
+        free_plan(P);
+        return rc;
+    }
+    P->pb_kx0 = V.klo_x;
+    P->pb_ky0 = V.klo_y;
+    P->pb_nkx = (int)(V.khi_x - V.klo_x + 1);
+    P->pb_nky = (int)(V.khi_y - V.klo_y + 1);
+    const size_t npb = (size_t)P->pb_nkx * P->pb_nky, npix = (size_t)P->nx * P->ny;
+    P->fixed_bytes = npb * 12 + npix * 12 + npix * 32;
+    if (P->budget && P->fixed_bytes > P->budget) {
+        free_plan(P);
+        return NUFDS_ENOMEM;
+    }
+    if (cudaMalloc(&P->pb_base, npb * sizeof(short2)) != cudaSuccess ||
+        cudaMalloc(&P->pb_frac, npb * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&P->rm_base, npix * sizeof(short2)) != cudaSuccess ||
+        cudaMalloc(&P->rm_frac, npix * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&P->G, 4 * npix * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(P);
+        return NUFDS_ENOMEM;
+    }
+    // FP64 tables: inverse stretch on the full-view band; output map on the
+    // full-view pixel lattice (computed at z = 1, valid at every z)
+    const double B1 = full_width(P->lam, P->pitch, 1.0);
+    if ((rc = launch_pullback_table(P->lam, P->pitch, P->nx, P->ny, P->pb_kx0, P->pb_nkx,
+                                    P->pb_ky0, P->pb_nky, P->pb_base, P->pb_frac, st)) ||
+        (rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, 1.0, 0.0, 0.0, B1 / P->nx,
+                                 B1 / P->ny, P->nx, P->ny, P->rm_base, P->rm_frac, st))) {
+        free_plan(P);
+        return rc;
+    }
+    if (d_holo && (rc = load_impl(P, d_holo, st))) {
+        free_plan(P);
+        return rc;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(P);
+        return NUFDS_ECUDA;
+    }
+    *out = P;
+    return NUFDS_OK;
+}
+
+int nufds_plan_load(nufds_plan *P, const void *d_holo, void *stream) {
+    if (!P || !d_holo) return NUFDS_EINVAL;
+    return load_impl(P, d_holo, (cudaStream_t)stream);
+}
+
+int nufds_view_plan(const nufds_params *prm, const nufds_view *v, nufds_view_info *info) {
+    if (!prm || !v || !info) return NUFDS_EINVAL;
+    if (!(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
+        !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->nx <= 0 || prm->ny <= 0)
+        return NUFDS_EINVAL;
+    ViewPlan V;
+    Geom g = {prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny};
+    int rc = plan_view_impl(&g, v, &V);
+    if (rc) return rc;
+    memset(info, 0, sizeof *info);
+    info->out_nx = V.ox;
+    info->out_ny = V.oy;
+    info->k_lo_x = V.klo_x;
+    info->k_hi_x = V.khi_x;
+    info->k_lo_y = V.klo_y;
+    info->k_hi_y = V.khi_y;
+    info->np_x = V.npx;
+    info->np_y = V.npy;
+    info->k_c_x = V.kc_x;
+    info->k_c_y = V.kc_y;
+    info->pitch_out_x_m = V.px;
+    info->pitch_out_y_m = V.py;
+    info->width_m = V.w;
+    info->height_m = V.h;
+    info->on_full_view_lattice = V.lattice ? 1 : 0;
+    const size_t np = (size_t)V.npx * V.npy;
+    info->workspace_bytes = sizeof(float2) * 6 * np;
+    return NUFDS_OK;
+}
+
+int nufds_reconstruct(nufds_plan *P, const nufds_view *v, void *d_out, void *stream) {
+    return reconstruct_impl(P, v, d_out, (cudaStream_t)stream);
+}
+
+int nufds_reconstruct_batch(nufds_plan *const *plans, const nufds_view *views,
+                            void *const *d_outs, int32_t count, void *stream, int32_t *statuses) {
+    if (count < 0 || (count > 0 && (!plans || !views || !d_outs))) return NUFDS_EINVAL;
+    int first = NUFDS_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        int rc = reconstruct_impl(plans[i], &views[i], d_outs[i], (cudaStream_t)stream);
+        if (statuses) statuses[i] = rc;
+        if (rc && first == NUFDS_OK) first = rc;
+    }
+    return first;
+}
+
+void nufds_destroy(nufds_plan *P) {
+    if (!P) return;
+    cudaDeviceSynchronize();
+    free_plan(P);
+}
+
+uint64_t nufds_plan_device_bytes(const nufds_plan *P) {
+    if (!P) return 0;
+    return P->fixed_bytes + P->ws_bytes;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// The two off-grid resampling steps of NU-FDS as gathers on 2x oversampled grids.
+//
+// Step two (Section 4): S(f'_k) = H~(f(f'_k)), the hologram spectrum at the
+// pulled-back frequency of every stretched-lattice point, i.e. the DTFT of
+// the hologram evaluated off its DFT grid.  The spectrum is cached on a 2x
+// oversampled grid of the deapodised hologram, so the value at any frequency
+// is a short separable sum with the ES kernel (W x W taps).
+//
+// Step five: O(x_o) = O'(x_o'(x_o)), the Fresnel-transform output evaluated
+// at the Eq. 17 image of every output pixel, from the 2x oversampled FrT grid
+// the same way; then |O|^2 or O times the output chirp.
+//
+// Both read a coordinate table (integer fine-grid base + FP32 fraction,
+// derived in FP64) and wrap indices periodically (the DTFT is periodic).
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace nufds {
+
+__device__ __forceinline__ float es_weight(float d) {
+    // psi(d) = exp(beta (sqrt(1 - (2d/W)^2) - 1)), 0 outside |d| <= W/2
+    float t = d * (2.0f / kW);
+    float q = 1.0f - t * t;
+    return q > 0.0f ? expf((float)kBeta * (sqrtf(q) - 1.0f)) : 0.0f;
+}
+
+__device__ __forceinline__ int wrap(int m, int M) {
+    m %= M;
+    return m < 0 ? m + M : m;
+}
+
+__global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
+    const int jy = blockIdx.x * 32 + threadIdx.x;
+    const int jx = blockIdx.y * 8 + threadIdx.y;
+    if (jx >= a.npx || jy >= a.npy) return;
+    const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
+    float2 acc = make_float2(0.f, 0.f);
+    if (kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
+        const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
+        const short2 b = a.pb_base[t];
+        if (b.x != kMasked) {
+            const float2 f = a.pb_frac[t];
+            const int Mx = 2 * a.Nx, My = 2 * a.Ny;
+            float wx[kW], wy[kW];
+#pragma unroll
+            for (int i = 0; i < kW; ++i) {
+                wx[i] = es_weight(f.x + (kW / 2 - 1 - i));
+                wy[i] = es_weight(f.y + (kW / 2 - 1 - i));
+            }
+            const int mx0 = b.x - kW / 2 + 1 + a.Nx, my0 = b.y - kW / 2 + 1 + a.Ny;
+            int cols[kW];
+#pragma unroll
+            for (int j = 0; j < kW; ++j) cols[j] = wrap(my0 + j, My);
+#pragma unroll
+            for (int i = 0; i < kW; ++i) {
+                const float2 *row = a.G + (long)wrap(mx0 + i, Mx) * My;
+                float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < kW; ++j) {
+                    float2 g = __ldg(row + cols[j]);
+                    r.x = fmaf(wy[j], g.x, r.x);
+                    r.y = fmaf(wy[j], g.y, r.y);
+                }
+                acc.x = fmaf(wx[i], r.x, acc.x);
+                acc.y = fmaf(wx[i], r.y, acc.y);
+            }
+            // (-1)^(jx + jy): centring of the inverse transforms that follow
+            if ((jx + jy) & 1) acc = make_float2(-acc.x, -acc.y);
+        }
+    }
+    a.S[(long)jx * a.npy + jy] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    if (i >= a.ox || j >= a.oy) return;
+    const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
+    const short2 b = a.rm_base[t];
+    const float2 f = a.rm_frac[t];
+    const int Mx = 2 * a.npx, My = 2 * a.npy;
+    float wx[kW], wy[kW];
+#pragma unroll
+    for (int q = 0; q < kW; ++q) {
+        wx[q] = es_weight(f.x + (kW / 2 - 1 - q));
+        wy[q] = es_weight(f.y + (kW / 2 - 1 - q));
+    }
+    const int mx0 = (int)(b.x - 2 * a.kc_x) + a.npx - kW / 2 + 1;
+    const int my0 = (int)(b.y - 2 * a.kc_y) + a.npy - kW / 2 + 1;
+    int cols[kW];
+#pragma unroll
+    for (int q = 0; q < kW; ++q) cols[q] = wrap(mx0 + q, Mx);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < kW; ++p) {
+        const float2 *row = a.Q + (long)wrap(my0 + p, My) * Mx;
+        float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < kW; ++q) {
+            float2 g = __ldg(row + cols[q]);
+            r.x = fmaf(wx[q], g.x, r.x);
+            r.y = fmaf(wx[q], g.y, r.y);
+        }
+        acc.x = fmaf(wy[p], r.x, acc.x);
+        acc.y = fmaf(wy[p], r.y, acc.y);
+    }
+    const long o = (long)j * a.ox + i;
+    if (a.kind == 0) {
+        ((float *)a.out)[o] = fmaf(acc.x, acc.x, acc.y * acc.y);
+    } else {
+        // e^{i kappa t'^2} per axis, t' = (b + f) / 2: table for the b^2 part,
+        // FP32 for kappa (b f / 2 + f^2 / 4) (|.| < ~10 rad)
+        float2 ex = __ldg(a.Ex + (b.x - a.ex_b0)), ey = __ldg(a.Ey + (b.y - a.ey_b0));
+        float ph = a.kappa_x * (0.5f * (float)b.x * f.x + 0.25f * f.x * f.x) +
+                   a.kappa_y * (0.5f * (float)b.y * f.y + 0.25f * f.y * f.y);
+        float s, c;
+        sincosf(ph, &s, &c);
+        float2 e = make_float2(ex.x * ey.x - ex.y * ey.y, ex.x * ey.y + ex.y * ey.x);
+        float2 w = make_float2(e.x * c - e.y * s, e.x * s + e.y * c);
+        ((float2 *)a.out)[o] = make_float2(acc.x * w.x - acc.y * w.y, acc.x * w.y + acc.y * w.x);
+    }
+}
+
+int launch_stretch(const StretchArgs &a, cudaStream_t st) {
+    dim3 grid((a.npy + 31) / 32, (a.npx + 7) / 8);
+    k_stretch<<<grid, dim3(32, 8), 0, st>>>(a);
+    count_launch();
+    return check_launch();
+}
+
+int launch_remap(const RemapArgs &a, cudaStream_t st) {
+    dim3 grid((a.ox + 31) / 32, (a.oy + 7) / 8);
+    k_remap<<<grid, dim3(32, 8), 0, st>>>(a);
+    count_launch();
+    return check_launch();
+}
+
+}  // namespace nufds

@@ -1,0 +1,130 @@
+// Internal declarations shared by the CUDA sources of libnufds (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace nufds {
+
+// Interpolation kernel of the oversampled-grid resampling ("exponential of
+// semicircle", Barnett, Magland & af Klinteberg, SIAM J. Sci. Comput. 2019):
+//   psi(s) = exp(beta (sqrt(1 - (2 s / W)^2) - 1)),  |s| < W/2 fine cells.
+// Oversampling 2 in each axis.
+constexpr int kW = 8;
+constexpr double kBeta = 2.30 * kW;
+constexpr int kSigma = 2;
+
+struct c64 {
+    float x, y;
+};
+
+// Entry of a coordinate table: a point on a fine (2x oversampled) grid as
+// centred integer base (floor of 2t) and fraction in [0, 1).
+// base.x == kMasked marks a point that is zeroed.
+constexpr int16_t kMasked = -32768;
+
+// ---------------------------------------------------------------------------
+// Row FFT passes (fft_rows.cu)
+// ---------------------------------------------------------------------------
+constexpr int kMaxPasses = 8;
+
+struct FftPlan {
+    int L = 0;
+    int npass = 0;
+    int radix[kMaxPasses] = {};
+    int stride[kMaxPasses] = {};   // s_j = L / (r_1 ... r_j)
+    int prefix[kMaxPasses] = {};   // r_1 ... r_{j-1}
+    int threads = 0;
+    size_t smem_bytes = 0;
+    // device tables (owned by the length cache)
+    const float2 *tw_fine = nullptr;   // W_L^j, j < 64
+    const float2 *tw_coarse = nullptr; // W_L^{64 i}, i < ceil(L/64)
+    const float2 *mod1 = nullptr;      // e^{-i pi (n - L/2)/L}
+    const double *deapod = nullptr;    // 1 / psi_hat(n - L/2)
+    const float *pad_pre = nullptr;    // (-1)^n / psi_hat(n - L/2)
+};
+
+// Build (or fetch from the per-device cache) the plan and tables of length L.
+int fft_plan_get(int L, const FftPlan **out);
+
+// Padded forward pass: rows of length L (in, row stride in_ld elements) ->
+// rows of length 2L (out, row stride out_ld):
+//   out[r][2k + a] = (-1)^k sum_n in[r][n] pre[n] e^{-i pi a (n - L/2)/L} e^{-2 pi i n k/L}
+// with pre = pad_pre.  This is the centred DFT on the 2x oversampled grid of
+// the deapodised row.
+int launch_rows_pad2(const FftPlan &p, const float2 *in, long in_ld, float2 *out, long out_ld,
+                     int rows, cudaStream_t st);
+
+// View pass: rows of length L: inverse centred DFT (input already carries
+// (-1)^k), multiply by chirp[n] (complex, includes deapodisation and 1/L),
+// then the padded forward pass as above (output 2L per row).  scratch holds
+// grid-size * L float2.
+int launch_rows_view(const FftPlan &p, const float2 *in, long in_ld, const float2 *chirp,
+                     float2 *out, long out_ld, int rows, float2 *scratch, int grid,
+                     cudaStream_t st);
+int rows_view_grid(const FftPlan &p, int rows);
+
+// out[c][r] = in[r][c]
+int launch_transpose(const float2 *in, long in_ld, float2 *out, long out_ld, int rows, int cols,
+                     cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// FP64 maps and tables (maps.cu)
+// ---------------------------------------------------------------------------
+double host_g(double s);                       // int_0^s (1 - t^2)^(-3/4) dt
+void host_phi(double u, double v, double *up, double *vp);  // stretch of Eqs. 9, 10, 16
+double g_at_one();
+
+// Pull-back table over lattice [kx0, kx0+nkx) x [ky0, ky0+nky), layout [kx][ky].
+int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
+                          int nky, short2 *base, float2 *frac, cudaStream_t st);
+// Output-map table for pixels x_o = cx + (i - ox/2) px etc. at distance z,
+// layout [j][i]; t' in stretched-lattice units, stored as floor(2t') + frac.
+int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
+                       double px, double py, int ox, int oy, short2 *base, float2 *frac,
+                       cudaStream_t st);
+// chirp[n] = e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) N pitch / L
+int launch_chirp_table(const double *deapod, int L, double window_m, double lam, double z,
+                       float2 *chirp, cudaStream_t st);
+// Output chirp pieces: E[b - b0] = e^{i kappa b^2 / 4} for b in [b0, b0 + nb)
+int launch_outchirp_table(double kappa, long b0, int nb, float2 *E, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Gathers (gather.cu)
+// ---------------------------------------------------------------------------
+struct StretchArgs {
+    const float2 *G;        // oversampled spectrum, layout [mx][my], 2Nx x 2Ny
+    int Nx, Ny;
+    const short2 *pb_base;  // pull-back table, layout [kx][ky]
+    const float2 *pb_frac;
+    long pb_kx0, pb_ky0;
+    int pb_nkx, pb_nky;
+    long klo_x, khi_x, klo_y, khi_y, kc_x, kc_y;
+    int npx, npy;
+    float2 *S;              // output, layout [jx][jy], npx x npy
+};
+int launch_stretch(const StretchArgs &a, cudaStream_t st);
+
+struct RemapArgs {
+    const float2 *Q;        // oversampled FrT output, layout [my][mx], 2npy x 2npx
+    int npx, npy;
+    long kc_x, kc_y;
+    const short2 *rm_base;  // output-map table, layout [j][i], row length rm_ld
+    const float2 *rm_frac;
+    long rm_ld, rm_i0, rm_j0;
+    int ox, oy;
+    int kind;               // 0 intensity f32, 1 field c64
+    const float2 *Ex, *Ey;  // output chirp tables (field only)
+    long ex_b0, ey_b0;
+    float kappa_x, kappa_y;
+    void *out;
+};
+int launch_remap(const RemapArgs &a, cudaStream_t st);
+
+// launch bookkeeping
+void count_launch();
+int check_launch();
+
+}  // namespace nufds

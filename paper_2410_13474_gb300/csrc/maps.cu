@@ -1,0 +1,244 @@
+// FP64 coordinate maps of the NU-FDS method and the tables built from them.
+//
+// With u = lambda f_x, v = lambda f_y, the stretch of Eqs. 9, 10 with the
+// magnification of Eq. 16 reads
+//   lambda f_x' = (1 - v^2)^(1/4) g(u / sqrt(1 - v^2)),
+//   lambda f_y' = (1 - u^2)^(1/4) g(v / sqrt(1 - u^2)),
+// where g(s) = s 2F1(1/2, 3/4; 3/2; s^2) = int_0^s (1 - t^2)^(-3/4) dt
+// (integrating Eq. 15 in f_x).  g is evaluated from two series of that
+// integral: the binomial series of the integrand around t = 0 for |s| <= 3/4,
+// and around t = 1 (in powers of 1 - s) above, with g(1) = B(1/2, 1/4) / 2.
+//
+// Every value that sets a sampling position is computed here in FP64, once
+// per plan (or per off-lattice view), and stored as an integer base on the
+// 2x oversampled grid plus an FP32 fraction in [0, 1), which keeps ~1e-7 of
+// a fine cell after the FP32 kernels take over.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace nufds {
+
+__host__ __device__ inline double g_series(double s, double g1) {
+    double a = fabs(s);
+    double r;
+    if (a <= 0.75) {
+        // sum_n c_n s^(2n+1) / (2n+1), c_n = (3/4)_n / n!
+        double s2 = a * a, p = a, c = 1.0, sum = a;
+        for (int n = 1; n < 200; ++n) {
+            c *= (n - 0.25) / n;
+            p *= s2;
+            double t = c * p / (2.0 * n + 1.0);
+            sum += t;
+            if (t < 1e-18 * sum) break;
+        }
+        r = sum;
+    } else {
+        // g(1) - 2^(-3/4) sum_n c_n 2^(-n) e^(n + 1/4) / (n + 1/4), e = 1 - s
+        double e = 1.0 - a;
+        if (e <= 0.0) {
+            r = g1;
+        } else {
+            double q = sqrt(sqrt(e)), c = 1.0, h = 1.0, sum = 0.0;
+            for (int n = 0; n < 200; ++n) {
+                if (n > 0) {
+                    c *= (n - 0.25) / n;
+                    h *= 0.5 * e;
+                }
+                double t = c * h * q / (n + 0.25);
+                sum += t;
+                if (t < 1e-18 * sum) break;
+            }
+            r = g1 - 0.59460355750136053336 * sum;  // 2^(-3/4)
+        }
+    }
+    return s < 0 ? -r : r;
+}
+
+double g_at_one() {
+    // B(1/2, 1/4) / 2 = Gamma(1/2) Gamma(1/4) / (2 Gamma(3/4))
+    return tgamma(0.5) * tgamma(0.25) / (2.0 * tgamma(0.75));
+}
+
+double host_g(double s) { return g_series(s, g_at_one()); }
+
+__host__ __device__ inline void phi_uv(double u, double v, double g1, double *up, double *vp) {
+    double ay = 1.0 - v * v, ax = 1.0 - u * u;
+    *up = sqrt(sqrt(ay)) * g_series(u / sqrt(ay), g1);
+    *vp = sqrt(sqrt(ax)) * g_series(v / sqrt(ax), g1);
+}
+
+void host_phi(double u, double v, double *up, double *vp) { phi_uv(u, v, g_at_one(), up, vp); }
+
+// Jacobian d(u', v')/d(u, v) of the stretch (Eq. 15 on the diagonal).
+__device__ inline void jac_uv(double u, double v, double g1, double J[4]) {
+    double ay = 1.0 - v * v, ax = 1.0 - u * u, r = 1.0 - u * u - v * v;
+    double r34 = 1.0 / sqrt(sqrt(r * r * r));  // r^(-3/4)
+    J[0] = sqrt(ay) * r34;
+    J[3] = sqrt(ax) * r34;
+    double gy = g_series(u / sqrt(ay), g1), gx = g_series(v / sqrt(ax), g1);
+    J[1] = -0.5 * v * gy / sqrt(sqrt(ay * ay * ay)) + u * v * r34 / sqrt(ay);
+    J[2] = -0.5 * u * gx / sqrt(sqrt(ax * ax * ax)) + u * v * r34 / sqrt(ax);
+}
+
+// Inverse of the stretch: solve phi(u, v) = (up, vp) inside the unit disc by
+// damped Newton.  Returns false when (up, vp) has no pre-image.
+__device__ bool pullback_uv(double up, double vp, double g1, double tol, double *uo, double *vo) {
+    double u = up, v = vp;
+    double rr = u * u + v * v;
+    if (rr > 0.81) {
+        double sc = 0.9 * rsqrt(rr);
+        u *= sc;
+        v *= sc;
+    }
+    double fu, fv;
+    phi_uv(u, v, g1, &fu, &fv);
+    double res = fabs(fu - up) + fabs(fv - vp);
+    for (int it = 0; it < 100; ++it) {
+        double J[4];
+        jac_uv(u, v, g1, J);
+        double det = J[0] * J[3] - J[1] * J[2];
+        double ru = up - fu, rv = vp - fv;
+        double du = (J[3] * ru - J[1] * rv) / det;
+        double dv = (J[0] * rv - J[2] * ru) / det;
+        double step = 1.0;
+        bool ok = false;
+        for (int h = 0; h < 60; ++h) {
+            double un = u + step * du, vn = v + step * dv;
+            if (un * un + vn * vn < 1.0) {
+                double gu, gv;
+                phi_uv(un, vn, g1, &gu, &gv);
+                double rn = fabs(gu - up) + fabs(gv - vp);
+                if (rn < res || rn == 0.0 || step * (fabs(du) + fabs(dv)) <= tol) {
+                    u = un;
+                    v = vn;
+                    fu = gu;
+                    fv = gv;
+                    res = rn;
+                    ok = true;
+                    break;
+                }
+            }
+            step *= 0.5;
+        }
+        if (!ok) return false;
+        if (step * (fabs(du) + fabs(dv)) <= tol) {
+            *uo = u;
+            *vo = v;
+            return res <= 2e-12 * (1.0 + fabs(up) + fabs(vp));
+        }
+    }
+    return false;
+}
+
+__device__ inline void split_fine(double t2, short *base, float *frac) {
+    double b = floor(t2);
+    *base = (short)b;
+    *frac = (float)(t2 - b);
+}
+
+// Table of f(f'_k) for lattice points k of the stretched band, layout [kx][ky]:
+// fine coordinates 2 t with t = N pitch f (centred grid units).  Masked where
+// there is no pre-image or |t_x| > N_x/2 or |t_y| > N_y/2.
+__global__ void k_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx,
+                                 long ky0, int nky, double g1, short2 *base, float2 *frac) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nkx * nky) return;
+    int ix = (int)(idx / nky), iy = (int)(idx - (long)ix * nky);
+    double up = lam * (double)(kx0 + ix) / (nx * pitch);
+    double vp = lam * (double)(ky0 + iy) / (ny * pitch);
+    double u, v;
+    short2 b = make_short2(kMasked, kMasked);
+    float2 f = make_float2(0.f, 0.f);
+    if (pullback_uv(up, vp, g1, 1e-13 * lam / pitch, &u, &v)) {
+        double tx = nx * pitch * u / lam, ty = ny * pitch * v / lam;
+        if (fabs(tx) <= 0.5 * nx && fabs(ty) <= 0.5 * ny) {
+            split_fine(2.0 * tx, &b.x, &f.x);
+            split_fine(2.0 * ty, &b.y, &f.y);
+        }
+    }
+    base[idx] = b;
+    frac[idx] = f;
+}
+
+// Output map of Eq. 17 in stretched-lattice units t' = N pitch f_0 m(f_0),
+// f_0 = (x_o, y_o) / (lambda R_0), for view pixels; layout [j][i].
+__global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z, double cx,
+                              double cy, double px, double py, int ox, int oy, double g1,
+                              short2 *base, float2 *frac) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)ox * oy) return;
+    int j = (int)(idx / ox), i = (int)(idx - (long)j * ox);
+    double xo = cx + (i - 0.5 * ox) * px, yo = cy + (j - 0.5 * oy) * py;
+    double R0 = sqrt(xo * xo + yo * yo + z * z);
+    double up, vp;
+    phi_uv(xo / R0, yo / R0, g1, &up, &vp);
+    double tx = nx * pitch * up / lam, ty = ny * pitch * vp / lam;
+    short2 b;
+    float2 f;
+    split_fine(2.0 * tx, &b.x, &f.x);
+    split_fine(2.0 * ty, &b.y, &f.y);
+    base[idx] = b;
+    frac[idx] = f;
+}
+
+// chirp[n] = e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) window / L
+__global__ void k_chirp_table(const double *deapod, int L, double window, double lam, double z,
+                              float2 *chirp) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L) return;
+    double x = (n - L / 2) * (window / L);
+    double ph = M_PI * x * x / (lam * z);
+    ph -= 2.0 * M_PI * rint(ph / (2.0 * M_PI));
+    double s, c;
+    sincos(ph, &s, &c);
+    double a = deapod[n] / L;
+    chirp[n] = make_float2((float)(c * a), (float)(s * a));
+}
+
+__global__ void k_outchirp_table(double kappa, long b0, int nb, float2 *E) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    double b = (double)(b0 + i);
+    double ph = 0.25 * kappa * b * b;
+    ph -= 2.0 * M_PI * rint(ph / (2.0 * M_PI));
+    double s, c;
+    sincos(ph, &s, &c);
+    E[i] = make_float2((float)c, (float)s);
+}
+
+int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
+                          int nky, short2 *base, float2 *frac, cudaStream_t st) {
+    long n = (long)nkx * nky;
+    if (n <= 0) return 0;
+    k_pullback_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lam, pitch, nx, ny, kx0, nkx,
+                                                                 ky0, nky, g_at_one(), base, frac);
+    count_launch();
+    return check_launch();
+}
+
+int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
+                       double px, double py, int ox, int oy, short2 *base, float2 *frac,
+                       cudaStream_t st) {
+    long n = (long)ox * oy;
+    if (n <= 0) return 0;
+    k_remap_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lam, pitch, nx, ny, z, cx, cy, px,
+                                                              py, ox, oy, g_at_one(), base, frac);
+    count_launch();
+    return check_launch();
+}
+
+int launch_chirp_table(const double *deapod, int L, double window_m, double lam, double z,
+                       float2 *chirp, cudaStream_t st) {
+    k_chirp_table<<<(L + 255) / 256, 256, 0, st>>>(deapod, L, window_m, lam, z, chirp);
+    count_launch();
+    return check_launch();
+}
+
+int launch_outchirp_table(double kappa, long b0, int nb, float2 *E, cudaStream_t st) {
+    k_outchirp_table<<<(nb + 255) / 256, 256, 0, st>>>(kappa, b0, nb, E);
+    count_launch();
+    return check_launch();
+}
+
+}  // namespace nufds
