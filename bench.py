@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the NU-FDS reconstruction hot path on GB300.
+
+One step = one cold reconstruction of a new hologram of the workload's
+geometry: the oversampled spectrum of the hologram (FFT2), the non-uniform
+stretch, the FFT-based Fresnel transform at the requested distance and the
+output remap, i.e. plan.load(hologram) + plan.reconstruct(full view).  The
+per-geometry FP64 tables (the paper's initialisation steps) are built once,
+before the timed region, and reported as init_ms.
+
+Default workload: 16384^2 complex64 point-cloud hologram, 532 nm, 0.307 um
+pitch (120 deg FoV), 20000 seeded points in z in [2, 10] mm, full 16384^2
+intensity view at z = 6 mm.  Inputs (2 GiB hologram, 8.6 GB spectrum) exceed
+L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "16K UWA Mpix/s & HBM roofline frac vs plain FP32; p50/p99 view latency"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _workload(name):
+    from synth import configs
+    return {"uwa16k": configs.UWA_16K, "wa4096": configs.WA_4096, "small512": configs.SMALL_512}[name]
+
+
+def _config(w, extra=None):
+    c = {"workload": w.name, "hologram": "%dx%d complex64" % (w.n, w.n),
+         "wavelength_nm": round(w.wavelength * 1e9, 3), "pitch_um": round(w.pitch * 1e6, 4),
+         "points": w.n_points, "z_points_mm": [w.z_range[0] * 1e3, w.z_range[1] * 1e3],
+         "view": "full %dx%d intensity at z = %g mm" % (w.n, w.n, w.z_view * 1e3),
+         "step": "FFT2 of a new hologram + stretch + FrT + remap (tables built once)",
+         "l2_flush": "none: inputs larger than L2 (hologram %.1f GiB, spectrum %.1f GiB)"
+                     % (8 * w.n * w.n / 2 ** 30, 32 * w.n * w.n / 2 ** 30),
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic(stage):
+    """dram bytes per launch of `stage` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    from paper_2410_13474_gb300 import build as b
+    if d.get("sources_sha256") != b.sources_digest():
+        return None
+    e = d.get("kernels", {}).get(stage)
+    return None if e is None else e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(w, min_seconds=10.0, n=1024):
+    """The FP64 oracle as it stands on the host cores: full-view reconstruction
+    of an n x n hologram of the workload's geometry (its central crop), repeated
+    until min_seconds of work; Mpix/s of output."""
+    import oracle
+    import synth
+    pts = w.point_cloud()[:500]
+    H = synth.hologram(pts, w.wavelength, w.pitch, n, n)
+    times = []
+    t_all = time.time()
+    while True:
+        t = time.time()
+        oracle.reconstruct(H, w.wavelength, w.pitch, w.z_view)
+        times.append(time.time() - t)
+        if time.time() - t_all >= min_seconds:
+            break
+    s = statistics.mean(times)
+    return {"value": round(n * n / s / 1e6, 6), "unit": "Mpix/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "FP64 oracle, full-view reconstruction of the central %dx%d crop of the "
+                      "workload geometry (same wavelength, pitch, z; hologram of 500 of its points), "
+                      "%d runs, mean %.2f s each" % (n, n, len(times), s)}
+
+
+def run_reference(args, w):
+    """The oracle timed as the reference arm (host cores, bounded sample per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    n = 512
+    pts = w.point_cloud()[:500]
+    H = synth.hologram(pts, w.wavelength, w.pitch, n, n)
+    for _ in range(args.warmup):
+        oracle.reconstruct(H, w.wavelength, w.pitch, w.z_view)
+    t = time.time()
+    for _ in range(args.steps):
+        oracle.reconstruct(H, w.wavelength, w.pitch, w.z_view)
+    dt = (time.time() - t) / args.steps
+    val = n * n / dt / 1e6
+    sample = ("FP64 oracle on the host cores, one step = full-view reconstruction of the central "
+              "%dx%d crop of the workload geometry (same wavelength, pitch, z)" % (n, n))
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "Mpix/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w, {"sample": sample}),
+            "e2e": {"value": round(val, 6), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": round(val, 6), "unit": "Mpix/s", "kind": "oracle",
+                             "cores": oracle.num_threads(), "sample": sample},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2410_13474_gb300 as nf
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2410_13474_gb300 import build as b
+    b.build()
+    stream = torch.cuda.current_stream()
+    n = w.n
+    pts = w.point_cloud()
+    t0 = time.time()
+    d_holo = synth.gpu_hologram(pts, w.wavelength, w.pitch, n, n)
+    gen_s = time.time() - t0
+    torch.cuda.synchronize()
+    t0 = time.time()
+    plan = nf.Plan(w.wavelength, w.pitch, n, n)
+    torch.cuda.synchronize()
+    init_ms = (time.time() - t0) * 1e3
+    view = nf.View(z=w.z_view)
+    out = plan.output_like(view)
+    info = plan.view_plan(view)
+
+    def step():
+        plan.load(d_holo)
+        plan.reconstruct(view, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.profile(True)
+    nf.launch_count(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = nf.launch_count()
+    plan.profile(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clk = clocks.stop()
+    stats = plan.profile_read()
+
+    # end to end through the public API with host buffers
+    h_holo = torch.empty((n, n), dtype=torch.complex64, pin_memory=True)
+    h_holo.copy_(d_holo)
+    h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+    d_in = torch.empty_like(d_holo)
+
+    def step_e2e():
+        d_in.copy_(h_holo, non_blocking=True)
+        plan.load(d_in)
+        plan.reconstruct(view, out)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_e2e()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = ev0.elapsed_time(ev1) / args.steps
+
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    pix = info["out_nx"] * info["out_ny"]
+    value = world * pix / (ms * 1e-3) / 1e6
+    value_e2e = world * pix / (ms_e2e * 1e-3) / 1e6
+
+    dom = max(stats, key=lambda s: s["total_ms"])
+    per_launch_bytes = dom["bytes"] / dom["launches"]
+    per_launch_ms = dom["total_ms"] / dom["launches"]
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+            "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": _traffic(dom["name"]),
+            "bytes_per_launch": per_launch_bytes, "ms_per_launch": round(per_launch_ms, 4)}
+    stages = {s["name"]: {"ms_per_step": round(s["total_ms"] / args.steps, 4),
+                          "GBps": round(s["bytes"] / (s["total_ms"] * 1e-3) / 1e9, 1)
+                          if s["total_ms"] > 0 else None} for s in stats}
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(w, {"np": [info["np_x"], info["np_y"]]}),
+            "e2e": {"value": round(value_e2e, 2), "unit": "Mpix/s",
+                    "h2d_bytes_per_step": int(h_holo.numel() * 8),
+                    "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
+            "roofline": roof, "stages": stages, "clocks": clk, "gpu_launches": int(launches),
+            "init_ms": round(init_ms, 1), "input_gen_s": round(gen_s, 2)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uwa16k", choices=["uwa16k", "wa4096", "small512"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = _workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -147,6 +147,26 @@ uint64_t nufds_plan_device_bytes(const nufds_plan *plan);
 /* Static name of a status code. */
 const char *nufds_status_string(int status);
 
+/* Per-stage timing of the launches a plan issued while profiling was on. */
+typedef struct nufds_stage_stat {
+    char name[24];     /* stage name, e.g. "view_rows_x"                              */
+    int64_t launches;  /* kernel launches recorded                                    */
+    double total_ms;   /* summed CUDA-event durations of those launches (device time) */
+    double bytes;      /* summed algorithmic bytes: compulsory reads + writes         */
+} nufds_stage_stat;
+
+/*
+ * enable = 1: clear and start recording a CUDA event pair around every kernel
+ * the plan launches (on the launching stream); 0: stop recording.
+ */
+int nufds_profile(nufds_plan *plan, int32_t enable);
+
+/*
+ * Aggregate what was recorded, one entry per stage (at most max entries into
+ * out; *count receives the number of stages).  Waits for the recorded events.
+ */
+int nufds_profile_read(nufds_plan *plan, nufds_stage_stat *out, int32_t max, int32_t *count);
+
 /*
  * Number of kernel launches issued by this library on the calling thread
  * since the last reset (reset = 1 zeroes it after reading).  Lets a caller

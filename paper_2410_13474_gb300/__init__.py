@@ -25,7 +25,8 @@ OUT_INTENSITY, OUT_FIELD = 0, 1
 # every function include/nufds.h declares
 ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",
                  "nufds_reconstruct_batch", "nufds_destroy", "nufds_plan_device_bytes",
-                 "nufds_status_string", "nufds_launch_count")
+                 "nufds_status_string", "nufds_launch_count", "nufds_profile",
+                 "nufds_profile_read")
 
 
 class NufdsError(RuntimeError):
@@ -60,6 +61,11 @@ class _ViewInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_uint64)]
 
 
+class _StageStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -86,6 +92,9 @@ def lib():
         L.nufds_plan_device_bytes.restype = ctypes.c_uint64
         L.nufds_status_string.argtypes = [ctypes.c_int]
         L.nufds_status_string.restype = ctypes.c_char_p
+        L.nufds_profile.argtypes = [vp, ctypes.c_int32]
+        L.nufds_profile_read.argtypes = [vp, ctypes.POINTER(_StageStat), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32)]
         L.nufds_launch_count.argtypes = [ctypes.c_int32]
         L.nufds_launch_count.restype = ctypes.c_int64
         _lib = L
@@ -189,6 +198,19 @@ class Plan:
         _check(lib().nufds_reconstruct(self._p, ctypes.byref(v), ctypes.c_void_p(out.data_ptr()),
                                        _stream_handle(stream)), "nufds_reconstruct")
         return out
+
+    def profile(self, enable: bool = True):
+        """Start (clearing) or stop recording CUDA events around every launch."""
+        _check(lib().nufds_profile(self._p, 1 if enable else 0), "nufds_profile")
+
+    def profile_read(self) -> list:
+        """Per-stage [{name, launches, total_ms, bytes}] of what was recorded."""
+        arr = (_StageStat * 16)()
+        n = ctypes.c_int32()
+        _check(lib().nufds_profile_read(self._p, arr, 16, ctypes.byref(n)), "nufds_profile_read")
+        return [dict(name=arr[i].name.decode(), launches=int(arr[i].launches),
+                     total_ms=float(arr[i].total_ms), bytes=float(arr[i].bytes))
+                for i in range(min(n.value, 16))]
 
     def device_bytes(self) -> int:
         return int(lib().nufds_plan_device_bytes(self._p))

@@ -77,6 +77,18 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
     return LIB
 
 
+
+def sources_digest() -> str:
+    """sha256 over the CUDA sources and headers (ties profiles to the code they measured)."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
 if __name__ == "__main__":
     build(force=True, ptxas_verbose="--verbose-ptxas" in sys.argv, quiet=False)
     print(LIB)

@@ -15,6 +15,8 @@
 #include <list>
 #include <mutex>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "../../include/nufds.h"
 #include "internal.cuh"
@@ -66,11 +68,45 @@ struct nufds_plan {
     size_t ws_bytes = 0;
     size_t fixed_bytes = 0;
     std::list<std::pair<ViewKey, ViewPlan>> vcache;
+    // profiling: an event pair per recorded launch
+    bool prof = false;
+    struct Rec {
+        int stage;
+        double bytes;
+        int ev;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> events;
 };
 
 namespace nufds {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+enum Stage {
+    ST_PAD_ROWS_X, ST_PAD_TRANSPOSE, ST_PAD_ROWS_Y, ST_TABLES, ST_STRETCH, ST_VIEW_ROWS_Y,
+    ST_VIEW_TRANSPOSE, ST_VIEW_ROWS_X, ST_REMAP, ST_COUNT
+};
+static const char *kStageName[ST_COUNT] = {"pad_rows_x", "pad_transpose", "pad_rows_y",
+                                           "tables", "stretch", "view_rows_y",
+                                           "view_transpose", "view_rows_x", "remap"};
+
+// run one launch, bracketed by CUDA events on its stream when profiling
+template <class F>
+static int stage(nufds_plan *P, int st_id, double bytes, cudaStream_t st, F &&launch) {
+    if (!P->prof) return launch();
+    size_t k = P->recs.size();
+    while (P->events.size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return NUFDS_ECUDA;
+        P->events.push_back(e);
+    }
+    cudaEventRecord(P->events[2 * k], st);
+    int rc = launch();
+    cudaEventRecord(P->events[2 * k + 1], st);
+    P->recs.push_back({st_id, bytes, (int)k});
+    return rc;
+}
 
 static double full_width(double lam, double pitch, double z) {
     double st = lam / (2.0 * pitch);
@@ -252,12 +288,22 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
     if (rc) return rc;
     float2 *A = (float2 *)P->ws, *Bf = (float2 *)(P->ws + half);
     const float2 *H = (const float2 *)d_holo;
+    const double n2 = (double)P->nx * P->ny;
     // along x: rows of H (ny rows of nx) -> A (ny x 2nx)
-    if ((rc = launch_rows_pad2(*P->fx, H, P->nx, A, 2 * P->nx, P->ny, st))) return rc;
+    if ((rc = stage(P, ST_PAD_ROWS_X, 24.0 * n2, st, [&] {
+             return launch_rows_pad2(*P->fx, H, P->nx, A, 2 * P->nx, P->ny, st);
+         })))
+        return rc;
     // A (ny x 2nx) -> Bf (2nx x ny)
-    if ((rc = launch_transpose(A, 2 * P->nx, Bf, P->ny, P->ny, 2 * P->nx, st))) return rc;
+    if ((rc = stage(P, ST_PAD_TRANSPOSE, 32.0 * n2, st, [&] {
+             return launch_transpose(A, 2 * P->nx, Bf, P->ny, P->ny, 2 * P->nx, st);
+         })))
+        return rc;
     // along y: rows of Bf (2nx rows of ny) -> G (2nx x 2ny)
-    if ((rc = launch_rows_pad2(*P->fy, Bf, P->ny, P->G, 2 * P->ny, 2 * P->nx, st))) return rc;
+    if ((rc = stage(P, ST_PAD_ROWS_Y, 48.0 * n2, st, [&] {
+             return launch_rows_pad2(*P->fy, Bf, P->ny, P->G, 2 * P->ny, 2 * P->nx, st);
+         })))
+        return rc;
     P->loaded = true;
     return NUFDS_OK;
 }
@@ -300,20 +346,29 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
         rmf = (float2 *)p;
         rmb = (short2 *)(p + align256(sizeof(float2) * (size_t)V.ox * V.oy));
         rm_ld = V.ox;
-        if ((rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px, V.py,
-                                     V.ox, V.oy, rmb, rmf, st)))
+        if ((rc = stage(P, ST_TABLES, 12.0 * V.ox * V.oy, st, [&] {
+                 return launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px,
+                                           V.py, V.ox, V.oy, rmb, rmf, st);
+             })))
             return rc;
     }
     // chirp tables (FP64 phases), window N pitch, x_n = (n - N'/2) N pitch / N'
-    if ((rc = launch_chirp_table(fpx->deapod, V.npx, P->nx * P->pitch, P->lam, V.z, chx, st)))
+    if ((rc = stage(P, ST_TABLES, 16.0 * V.npx, st, [&] {
+             return launch_chirp_table(fpx->deapod, V.npx, P->nx * P->pitch, P->lam, V.z, chx, st);
+         })))
         return rc;
-    if ((rc = launch_chirp_table(fpy->deapod, V.npy, P->ny * P->pitch, P->lam, V.z, chy, st)))
+    if ((rc = stage(P, ST_TABLES, 16.0 * V.npy, st, [&] {
+             return launch_chirp_table(fpy->deapod, V.npy, P->ny * P->pitch, P->lam, V.z, chy, st);
+         })))
         return rc;
     const double kx = M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch));
     const double ky = M_PI * P->lam * V.z / ((P->ny * P->pitch) * (P->ny * P->pitch));
     if (v->out_kind == NUFDS_OUT_FIELD_C64) {
-        if ((rc = launch_outchirp_table(kx, W.ex_b0, W.nbx, Ex, st))) return rc;
-        if ((rc = launch_outchirp_table(ky, W.ey_b0, W.nby, Ey, st))) return rc;
+        if ((rc = stage(P, ST_TABLES, 8.0 * (W.nbx + W.nby), st, [&] {
+                 int r = launch_outchirp_table(kx, W.ex_b0, W.nbx, Ex, st);
+                 return r ? r : launch_outchirp_table(ky, W.ey_b0, W.nby, Ey, st);
+             })))
+            return rc;
     }
     // step two: stretch gather -> S_T in Bf (npx x npy)
     StretchArgs sa;
@@ -335,14 +390,29 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     sa.npx = V.npx;
     sa.npy = V.npy;
     sa.S = Bf;
-    if ((rc = launch_stretch(sa, st))) return rc;
+    const double np2 = (double)V.npx * V.npy;
+    const double nbx = (double)(V.khi_x - V.klo_x + 1), nby = (double)(V.khi_y - V.klo_y + 1);
+    // algorithmic bytes of the gather: table entries of the band, the part of
+    // G the band pulls back to (in proportion to the full band), S written
+    const double g_frac = (nbx * nby) / ((double)P->pb_nkx * P->pb_nky);
+    const double st_bytes = 12.0 * nbx * nby + 32.0 * P->nx * P->ny * g_frac + 8.0 * np2;
+    if ((rc = stage(P, ST_STRETCH, st_bytes, st, [&] { return launch_stretch(sa, st); })))
+        return rc;
     // steps two/three along y: S_T rows (npx of npy) -> A (npx x 2npy)
-    if ((rc = launch_rows_view(*fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y, st)))
+    if ((rc = stage(P, ST_VIEW_ROWS_Y, 24.0 * np2, st, [&] {
+             return launch_rows_view(*fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y, st);
+         })))
         return rc;
     // A (npx x 2npy) -> Bf (2npy x npx)
-    if ((rc = launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, st))) return rc;
+    if ((rc = stage(P, ST_VIEW_TRANSPOSE, 32.0 * np2, st, [&] {
+             return launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, st);
+         })))
+        return rc;
     // along x: Bf rows (2npy of npx) -> A = Q (2npy x 2npx)
-    if ((rc = launch_rows_view(*fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr, W.grid_x, st)))
+    if ((rc = stage(P, ST_VIEW_ROWS_X, 48.0 * np2, st, [&] {
+             return launch_rows_view(*fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr,
+                                     W.grid_x, st);
+         })))
         return rc;
     // step five: remap
     RemapArgs ra;
@@ -366,7 +436,10 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ra.kappa_x = (float)kx;
     ra.kappa_y = (float)ky;
     ra.out = d_out;
-    return launch_remap(ra, st);
+    // Q region the view maps into, its table, the output
+    const double rm_bytes = 32.0 * nbx * nby + 12.0 * V.ox * V.oy +
+                            (v->out_kind == NUFDS_OUT_FIELD_C64 ? 8.0 : 4.0) * V.ox * V.oy;
+    return stage(P, ST_REMAP, rm_bytes, st, [&] { return launch_remap(ra, st); });
 }
 
 static void free_plan(nufds_plan *P) {
@@ -377,6 +450,7 @@ static void free_plan(nufds_plan *P) {
     cudaFree(P->rm_frac);
     cudaFree(P->G);
     cudaFree(P->ws);
+    for (cudaEvent_t e : P->events) cudaEventDestroy(e);
     delete P;
 }
 
@@ -543,6 +617,39 @@ void nufds_destroy(nufds_plan *P) {
     if (!P) return;
     cudaDeviceSynchronize();
     free_plan(P);
+}
+
+int nufds_profile(nufds_plan *P, int32_t enable) {
+    if (!P) return NUFDS_EINVAL;
+    if (enable) P->recs.clear();
+    P->prof = enable != 0;
+    return NUFDS_OK;
+}
+
+int nufds_profile_read(nufds_plan *P, nufds_stage_stat *out, int32_t max, int32_t *count) {
+    if (!P || !count || (max > 0 && !out)) return NUFDS_EINVAL;
+    nufds_stage_stat agg[ST_COUNT];
+    memset(agg, 0, sizeof agg);
+    for (const auto &r : P->recs) {
+        if (cudaEventSynchronize(P->events[2 * r.ev + 1]) != cudaSuccess) return NUFDS_ECUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P->events[2 * r.ev], P->events[2 * r.ev + 1]) != cudaSuccess)
+            return NUFDS_ECUDA;
+        agg[r.stage].launches += 1;
+        agg[r.stage].total_ms += ms;
+        agg[r.stage].bytes += r.bytes;
+    }
+    int n = 0;
+    for (int s = 0; s < ST_COUNT; ++s) {
+        if (!agg[s].launches) continue;
+        if (n < max) {
+            out[n] = agg[s];
+            strncpy(out[n].name, kStageName[s], sizeof(out[n].name) - 1);
+        }
+        ++n;
+    }
+    *count = n;
+    return NUFDS_OK;
 }
 
 uint64_t nufds_plan_device_bytes(const nufds_plan *P) {

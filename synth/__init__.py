@@ -98,3 +98,48 @@ def tan_half_fov(wavelength: float, pitch: float) -> float:
     """tan(asin(lambda / (2 pitch))): half-angle of the grating-equation FoV (Eq. 1)."""
     s = wavelength / (2.0 * pitch)
     return s / math.sqrt(1.0 - s * s)
+
+
+# --------------------------------------------------------------------------
+# GPU generator (large inputs): same model, FP64 tile-centre phases + FP32
+# in-tile offsets (~3e-5 rad per term); see pointcloud_gpu.cu.
+# --------------------------------------------------------------------------
+_SO_GPU = os.path.join(_HERE, "libsynth_gpu.so")
+_lib_gpu = None
+
+
+def build_gpu(force: bool = False) -> str:
+    src = os.path.join(_HERE, "pointcloud_gpu.cu")
+    if force or not os.path.exists(_SO_GPU) or os.path.getmtime(_SO_GPU) < os.path.getmtime(src):
+        import shutil
+        nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = _SO_GPU + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc, "-shared", "-O3", "-gencode", "arch=compute_103a,code=sm_103a",
+                               "-Xcompiler", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, _SO_GPU)
+    return _SO_GPU
+
+
+def gpu_hologram(pts: np.ndarray, wavelength: float, pitch: float, nx: int, ny: int, out=None):
+    """complex64 cuda tensor (ny, nx) of the point-source hologram, made on the GPU."""
+    import torch
+    global _lib_gpu
+    with _lock:
+        if _lib_gpu is None:
+            build_gpu()
+            L = ctypes.CDLL(_SO_GPU)
+            L.synth_gpu_hologram.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+            _lib_gpu = L
+    d_pts = torch.from_numpy(np.ascontiguousarray(pts, np.float64)).cuda()
+    if out is None:
+        out = torch.empty((ny, nx), dtype=torch.complex64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    rc = _lib_gpu.synth_gpu_hologram(ctypes.c_void_p(d_pts.data_ptr()), pts.shape[0], wavelength,
+                                     pitch, nx, ny, ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(st))
+    if rc:
+        raise RuntimeError("synth_gpu_hologram failed (%d)" % rc)
+    torch.cuda.synchronize()
+    return out
