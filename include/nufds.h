@@ -168,6 +168,32 @@ int nufds_profile(nufds_plan *plan, int32_t enable);
 int nufds_profile_read(nufds_plan *plan, nufds_stage_stat *out, int32_t max, int32_t *count);
 
 /*
+ * Allocation-free reconstruction of a small hologram (no counterpart in the
+ * paper; an interface for callers).  For callers that must not call
+ * cudaMalloc or cudaFree -- for example a display or capture loop whose
+ * device memory is reserved up front by another framework's allocator, or one
+ * that cannot take the device-wide synchronisation that cudaFree implies --
+ * this runs the whole path (FP64 geometry tables, the oversampled spectrum of
+ * d_hologram_c64, and the view) without allocating device memory.  All working
+ * memory (tables, spectrum, pass buffers and the per-CTA scratch rows of the
+ * view passes) lives in one 6 MiB array in the library's static device
+ * memory, which every GPU that loads the library holds until the process
+ * exits.  Limits: nx, ny <= 128, FFT size N' <= 256 per axis, and off-lattice
+ * views of at most 16384 pixels; larger requests return NUFDS_EUNSUPPORTED.
+ * Arguments, layouts and results are those of nufds_plan_create followed by
+ * nufds_reconstruct with the same params and view.
+ * The first call on a device looks up the array's device address there (do
+ * that first call before any stream capture).  Each call synchronises
+ * cuda_stream while it uploads its FFT tables, then enqueues its kernels.
+ * Every call uses the same array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.  No
+ * part of the array needs to start at zero; each kernel writes what the next
+ * one reads.
+ */
+int nufds_reconstruct_noalloc(const nufds_params *params, const nufds_view *view,
+                              const void *d_hologram_c64, void *d_out, void *cuda_stream);
+
+/*
  * Number of kernel launches issued by this library on the calling thread
  * since the last reset (reset = 1 zeroes it after reading).  Lets a caller
  * count the GPU work a call made.

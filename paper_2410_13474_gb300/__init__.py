@@ -26,7 +26,7 @@ OUT_INTENSITY, OUT_FIELD = 0, 1
 ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",
                  "nufds_reconstruct_batch", "nufds_destroy", "nufds_plan_device_bytes",
                  "nufds_status_string", "nufds_launch_count", "nufds_profile",
-                 "nufds_profile_read")
+                 "nufds_profile_read", "nufds_reconstruct_noalloc")
 
 
 class NufdsError(RuntimeError):

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <list>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -658,3 +659,210 @@ uint64_t nufds_plan_device_bytes(const nufds_plan *P) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free reconstruction for small holograms.
+//
+// Everything the reconstruction needs besides the caller's hologram and output
+// (tables, the oversampled spectrum, the pass buffers and the per-CTA scratch
+// rows of the view passes) lives in one file-scope device array.  Host code
+// only ever uses its device address from cudaGetSymbolAddress (taken once per
+// device, on the first call there); the symbol itself is a host-side stand-in.
+// ---------------------------------------------------------------------------
+namespace nufds {
+
+constexpr int kNoAllocMaxN = 128;        // hologram side
+constexpr int kNoAllocMaxNp = 256;       // FFT size N' of a view
+constexpr int kNoAllocMaxOutPix = 16384; // pixels of an off-lattice view
+constexpr size_t kNoAllocBytes = 6u << 20;
+
+static __device__ __align__(256) unsigned char g_noalloc_arena[kNoAllocBytes];
+
+static std::mutex g_noalloc_mu;
+static std::map<int, char *> g_noalloc_base;  // device -> address of g_noalloc_arena
+
+static int noalloc_base(char **out) {
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NUFDS_ECUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_base.find(dev);
+    if (it == g_noalloc_base.end()) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_arena) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return NUFDS_ECUDA;
+        }
+        it = g_noalloc_base.emplace(dev, (char *)p).first;
+    }
+    *out = it->second;
+    return NUFDS_OK;
+}
+
+struct Carver {
+    char *p;
+    size_t left;
+    template <class T> T *take(size_t count) {
+        size_t b = align256(sizeof(T) * count);
+        if (b > left) return nullptr;
+        T *r = (T *)p;
+        p += b;
+        left -= b;
+        return r;
+    }
+};
+
+static int noalloc_fft(Carver &c, int L, FftPlan *fp, cudaStream_t st) {
+    float2 *tw = c.take<float2>(64 + (L + 63) / 64 + L);
+    double *dea = c.take<double>(L);
+    float *pad = c.take<float>(L);
+    if (!tw || !dea || !pad) return NUFDS_EUNSUPPORTED;
+    int rc = fft_plan_fill(L, fp, tw, dea, pad, st);
+    return rc == -3 ? NUFDS_EUNSUPPORTED : (rc ? NUFDS_ECUDA : NUFDS_OK);
+}
+
+}  // namespace nufds
+
+extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_view *v,
+                                         const void *d_holo, void *d_out, void *stream) {
+    if (!prm || !v || !d_holo || !d_out) return NUFDS_EINVAL;
+    if (!(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
+        !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->reserved != 0 || prm->nx <= 0 ||
+        prm->ny <= 0 || prm->nx % 4 || prm->ny % 4)
+        return NUFDS_EINVAL;
+    if (prm->precision != NUFDS_FP32) return NUFDS_EUNSUPPORTED;
+    if (prm->nx > kNoAllocMaxN || prm->ny > kNoAllocMaxN || !fft_size_ok(prm->nx) ||
+        !fft_size_ok(prm->ny))
+        return NUFDS_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geom g = {prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny};
+    const int nx = prm->nx, ny = prm->ny;
+    ViewPlan F, V;
+    nufds_view fv;
+    memset(&fv, 0, sizeof fv);
+    fv.z_m = 1.0;
+    int rc;
+    if ((rc = plan_view_impl(&g, &fv, &F))) return rc;
+    if ((rc = plan_view_impl(&g, v, &V))) return rc;
+    if (V.npx > kNoAllocMaxNp || V.npy > kNoAllocMaxNp) return NUFDS_EUNSUPPORTED;
+    if (!V.lattice && (long)V.ox * V.oy > kNoAllocMaxOutPix) return NUFDS_EUNSUPPORTED;
+    const long pb_kx0 = F.klo_x, pb_ky0 = F.klo_y;
+    const int pb_nkx = (int)(F.khi_x - F.klo_x + 1), pb_nky = (int)(F.khi_y - F.klo_y + 1);
+    if (V.klo_x < pb_kx0 || V.khi_x >= pb_kx0 + pb_nkx || V.klo_y < pb_ky0 ||
+        V.khi_y >= pb_ky0 + pb_nky)
+        return NUFDS_EUNSUPPORTED;
+    char *base;
+    if ((rc = noalloc_base(&base))) return rc;
+    Carver c{base, kNoAllocBytes};
+    const size_t npix = (size_t)nx * ny, np2 = (size_t)V.npx * V.npy;
+    float2 *G = c.take<float2>(4 * npix);
+    short2 *pbb = c.take<short2>((size_t)pb_nkx * pb_nky);
+    float2 *pbf = c.take<float2>((size_t)pb_nkx * pb_nky);
+    short2 *rmb = c.take<short2>(npix);
+    float2 *rmf = c.take<float2>(npix);
+    float2 *A = c.take<float2>(4 * (np2 > npix ? np2 : npix));
+    float2 *Bf = c.take<float2>(2 * (np2 > npix ? np2 : npix));
+    float2 *chx = c.take<float2>(V.npx), *chy = c.take<float2>(V.npy);
+    if (!G || !pbb || !pbf || !rmb || !rmf || !A || !Bf || !chx || !chy) return NUFDS_EUNSUPPORTED;
+    FftPlan fx, fy, fpx, fpy;
+    if ((rc = noalloc_fft(c, nx, &fx, st)) || (rc = noalloc_fft(c, ny, &fy, st)) ||
+        (rc = noalloc_fft(c, V.npx, &fpx, st)) || (rc = noalloc_fft(c, V.npy, &fpy, st)))
+        return rc;
+    const int grid_y = rows_view_grid(fpy, V.npx), grid_x = rows_view_grid(fpx, 2 * V.npy);
+    const size_t sy = (size_t)grid_y * V.npy, sx = (size_t)grid_x * V.npx;
+    float2 *scr = c.take<float2>(sy > sx ? sy : sx);
+    const long ex_b0 = 2 * V.klo_x - 8, ey_b0 = 2 * V.klo_y - 8;
+    const int nbx = (int)(2 * (V.khi_x - V.klo_x) + 17), nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
+    float2 *Ex = nullptr, *Ey = nullptr;
+    if (v->out_kind == NUFDS_OUT_FIELD_C64) {
+        Ex = c.take<float2>(nbx);
+        Ey = c.take<float2>(nby);
+        if (!Ex || !Ey) return NUFDS_EUNSUPPORTED;
+    }
+    short2 *vrb = rmb;
+    float2 *vrf = rmf;
+    long rm_ld = nx, rm_i0 = 0, rm_j0 = 0;
+    if (V.lattice) {
+        rm_i0 = V.i0;
+        rm_j0 = V.j0;
+    } else {
+        vrb = c.take<short2>((size_t)V.ox * V.oy);
+        vrf = c.take<float2>((size_t)V.ox * V.oy);
+        rm_ld = V.ox;
+    }
+    if (!scr || !vrb || !vrf) return NUFDS_EUNSUPPORTED;
+    // geometry tables (FP64): inverse stretch on the full-view band, output map
+    const double B1 = full_width(g.lam, g.pitch, 1.0);
+    if ((rc = launch_pullback_table(g.lam, g.pitch, nx, ny, pb_kx0, pb_nkx, pb_ky0, pb_nky, pbb,
+                                    pbf, st)))
+        return rc;
+    if (V.lattice) {
+        if ((rc = launch_remap_table(g.lam, g.pitch, nx, ny, 1.0, 0.0, 0.0, B1 / nx, B1 / ny, nx,
+                                     ny, rmb, rmf, st)))
+            return rc;
+    } else if ((rc = launch_remap_table(g.lam, g.pitch, nx, ny, V.z, V.cx, V.cy, V.px, V.py, V.ox,
+                                        V.oy, vrb, vrf, st))) {
+        return rc;
+    }
+    // oversampled spectrum of the hologram
+    const float2 *H = (const float2 *)d_holo;
+    if ((rc = launch_rows_pad2(fx, H, nx, A, 2 * nx, ny, st)) ||
+        (rc = launch_transpose(A, 2 * nx, Bf, ny, ny, 2 * nx, st)) ||
+        (rc = launch_rows_pad2(fy, Bf, ny, G, 2 * ny, 2 * nx, st)))
+        return rc;
+    // the view
+    if ((rc = launch_chirp_table(fpx.deapod, V.npx, nx * g.pitch, g.lam, V.z, chx, st)) ||
+        (rc = launch_chirp_table(fpy.deapod, V.npy, ny * g.pitch, g.lam, V.z, chy, st)))
+        return rc;
+    const double kx = M_PI * g.lam * V.z / ((nx * g.pitch) * (nx * g.pitch));
+    const double ky = M_PI * g.lam * V.z / ((ny * g.pitch) * (ny * g.pitch));
+    if (v->out_kind == NUFDS_OUT_FIELD_C64 &&
+        ((rc = launch_outchirp_table(kx, ex_b0, nbx, Ex, st)) ||
+         (rc = launch_outchirp_table(ky, ey_b0, nby, Ey, st))))
+        return rc;
+    StretchArgs sa;
+    sa.G = G;
+    sa.Nx = nx;
+    sa.Ny = ny;
+    sa.pb_base = pbb;
+    sa.pb_frac = pbf;
+    sa.pb_kx0 = pb_kx0;
+    sa.pb_ky0 = pb_ky0;
+    sa.pb_nkx = pb_nkx;
+    sa.pb_nky = pb_nky;
+    sa.klo_x = V.klo_x;
+    sa.khi_x = V.khi_x;
+    sa.klo_y = V.klo_y;
+    sa.khi_y = V.khi_y;
+    sa.kc_x = V.kc_x;
+    sa.kc_y = V.kc_y;
+    sa.npx = V.npx;
+    sa.npy = V.npy;
+    sa.S = Bf;
+    if ((rc = launch_stretch(sa, st)) ||
+        (rc = launch_rows_view(fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, grid_y, st)) ||
+        (rc = launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, st)) ||
+        (rc = launch_rows_view(fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr, grid_x, st)))
+        return rc;
+    RemapArgs ra;
+    ra.Q = A;
+    ra.npx = V.npx;
+    ra.npy = V.npy;
+    ra.kc_x = V.kc_x;
+    ra.kc_y = V.kc_y;
+    ra.rm_base = vrb;
+    ra.rm_frac = vrf;
+    ra.rm_ld = rm_ld;
+    ra.rm_i0 = rm_i0;
+    ra.rm_j0 = rm_j0;
+    ra.ox = V.ox;
+    ra.oy = V.oy;
+    ra.kind = v->out_kind;
+    ra.Ex = Ex;
+    ra.Ey = Ey;
+    ra.ex_b0 = ex_b0;
+    ra.ey_b0 = ey_b0;
+    ra.kappa_x = (float)kx;
+    ra.kappa_y = (float)ky;
+    ra.out = d_out;
+    return launch_remap(ra, st);
+}

@@ -490,6 +490,76 @@ int fft_plan_get(int L, const FftPlan **out) {
     return 0;
 }
 
+// Plan and tables of length L written into caller-provided device memory
+// (no allocation): d_tw holds 64 + ceil(L/64) + L float2, d_deapod L doubles,
+// d_pad L floats.  Tables are computed on the host in FP64 and copied on st.
+int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pad,
+                  cudaStream_t st) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        int rc = init_constants();
+        if (rc) return rc;
+    }
+    int best[kMaxPasses], cur[kMaxPasses], best_n = kMaxPasses + 1;
+    factor(L, 0, nullptr, best_n, best, cur);
+    if (best_n > kMaxPasses || L < 16 || (L % 4)) return -3;
+    *p = FftPlan();
+    p->L = L;
+    p->npass = best_n;
+    int pre = 1, rem = L;
+    for (int j = 0; j < best_n; ++j) {
+        p->radix[j] = best[j];
+        p->prefix[j] = pre;
+        pre *= best[j];
+        rem /= best[j];
+        p->stride[j] = rem;
+    }
+    int t = (L / 16 + 31) / 32 * 32;
+    p->threads = t < 64 ? 64 : (t > 1024 ? 1024 : t);
+    p->smem_bytes = sizeof(float2) * (size_t)(L + L / 16 + 1);
+    if (p->smem_bytes > 48 * 1024) return -3;
+    int ncoarse = (L + 63) / 64;
+    std::vector<float2> h(64 + ncoarse + L);
+    for (int j = 0; j < 64; ++j) {
+        double a = -2.0 * M_PI * j / L;
+        h[j] = make_float2((float)cos(a), (float)sin(a));
+    }
+    for (int i = 0; i < ncoarse; ++i) {
+        double a = -2.0 * M_PI * (double)(64L * i % L) / L;
+        h[64 + i] = make_float2((float)cos(a), (float)sin(a));
+    }
+    for (int n = 0; n < L; ++n) {
+        double a = -M_PI * (n - L / 2) / (double)L;
+        h[64 + ncoarse + n] = make_float2((float)cos(a), (float)sin(a));
+    }
+    std::vector<double> ft;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        es_fourier(L, ft);
+    }
+    std::vector<double> dea(L);
+    std::vector<float> pp(L);
+    for (int n = 0; n < L; ++n) {
+        dea[n] = 1.0 / ft[n];
+        pp[n] = (float)((n & 1) ? -dea[n] : dea[n]);
+    }
+    if (cudaMemcpyAsync(d_tw, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_deapod, dea.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_pad, pp.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return -4;
+    // pageable sources: keep them alive until the copies have been consumed
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -4;
+    p->tw_fine = d_tw;
+    p->tw_coarse = d_tw + 64;
+    p->mod1 = d_tw + 64 + ncoarse;
+    p->deapod = d_deapod;
+    p->pad_pre = d_pad;
+    return 0;
+}
+
 static PassArgs pass_args(const FftPlan &p) {
     PassArgs a;
     a.L = p.L;

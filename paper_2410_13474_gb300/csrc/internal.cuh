@@ -48,6 +48,9 @@ struct FftPlan {
 
 // Build (or fetch from the per-device cache) the plan and tables of length L.
 int fft_plan_get(int L, const FftPlan **out);
+// Same plan with its tables written into caller-provided device memory.
+int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pad,
+                  cudaStream_t st);
 
 // Padded forward pass: rows of length L (in, row stride in_ld elements) ->
 // rows of length 2L (out, row stride out_ld):
