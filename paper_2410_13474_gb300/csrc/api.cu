@@ -355,11 +355,11 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     }
     // chirp tables (FP64 phases), window N pitch, x_n = (n - N'/2) N pitch / N'
     if ((rc = stage(P, ST_TABLES, 16.0 * V.npx, st, [&] {
-             return launch_chirp_table(fpx->deapod, V.npx, P->nx * P->pitch, P->lam, V.z, chx, st);
+             return launch_chirp_table(*fpx, P->nx * P->pitch, P->lam, V.z, chx, st);
          })))
         return rc;
     if ((rc = stage(P, ST_TABLES, 16.0 * V.npy, st, [&] {
-             return launch_chirp_table(fpy->deapod, V.npy, P->ny * P->pitch, P->lam, V.z, chy, st);
+             return launch_chirp_table(*fpy, P->ny * P->pitch, P->lam, V.z, chy, st);
          })))
         return rc;
     const double kx = M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch));
@@ -712,7 +712,7 @@ struct Carver {
 };
 
 static int noalloc_fft(Carver &c, int L, FftPlan *fp, cudaStream_t st) {
-    float2 *tw = c.take<float2>(64 + (L + 63) / 64 + L);
+    float2 *tw = c.take<float2>(fft_tw_count(L));
     double *dea = c.take<double>(L);
     float *pad = c.take<float>(L);
     if (!tw || !dea || !pad) return NUFDS_EUNSUPPORTED;
@@ -810,8 +810,8 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
         (rc = launch_rows_pad2(fy, Bf, ny, G, 2 * ny, 2 * nx, st)))
         return rc;
     // the view
-    if ((rc = launch_chirp_table(fpx.deapod, V.npx, nx * g.pitch, g.lam, V.z, chx, st)) ||
-        (rc = launch_chirp_table(fpy.deapod, V.npy, ny * g.pitch, g.lam, V.z, chy, st)))
+    if ((rc = launch_chirp_table(fpx, nx * g.pitch, g.lam, V.z, chx, st)) ||
+        (rc = launch_chirp_table(fpy, ny * g.pitch, g.lam, V.z, chy, st)))
         return rc;
     const double kx = M_PI * g.lam * V.z / ((nx * g.pitch) * (nx * g.pitch));
     const double ky = M_PI * g.lam * V.z / ((ny * g.pitch) * (ny * g.pitch));

@@ -20,9 +20,13 @@
 // come from a __constant__ table, also built in FP64.
 #include <math.h>
 
+#include <string.h>
+
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -151,160 +155,270 @@ template <int R, bool INV> struct Dft {
 // passes
 // ------------------------------------------------------------------------
 struct PassArgs {
-    int L, npass;
-    int radix[kMaxPasses], stride[kMaxPasses], prefix[kMaxPasses];
-    const float2 *tw_fine, *tw_coarse, *mod1;
-    const float *pad_pre;
+    int L, npass, ncoarse;
+    int radix[kMaxPasses], stride[kMaxPasses];
+    uint32_t mag_stride[kMaxPasses];  // ceil(2^32 / stride), 0 for stride 1
+    uint32_t mag_radix[kMaxPasses];   // ceil(2^32 / radix)
+    const float2 *tw;                 // fine[64] | coarse[ncoarse]: W_L^q = coarse[q>>6] fine[q&63]
+    const float2 *mod1, *mod1_slot;   // e^{-i pi (n - L/2)/L}: natural / slot order
+    const float *pad_pre;             // (-1)^n / psi_hat(n - L/2), natural order
 };
 
-__device__ __forceinline__ int phys(int p) { return p + (p >> 4); }
+// exact n / d for n * d < 2^32 (host check in fft_plan_*); m == 0 means d == 1
+__device__ __forceinline__ uint32_t udiv(uint32_t n, uint32_t m) { return m ? __umulhi(n, m) : n; }
 
-__device__ __forceinline__ float2 twiddle(const PassArgs &P, int q) {
-    return cmul(__ldg(P.tw_coarse + (q >> 6)), __ldg(P.tw_fine + (q & 63)));
+// shared-memory slot -> padded index (two-level padding: every 16th and 256th)
+__device__ __forceinline__ int phys(int p) { return p + (p >> 4) + (p >> 8); }
+
+__device__ __forceinline__ float2 tw_base(const float2 *tws, int q) {
+    return cmul(tws[64 + (q >> 6)], tws[q & 63]);
 }
 
-// natural index n -> DIF output / DIT input slot
-__device__ __forceinline__ int slot_of_index(const PassArgs &P, int n) {
-    int p = 0;
+// W[k] = w^k for k < R (W[0] unused) by a binary tree of products
+template <int R> __device__ __forceinline__ void tw_powers(float2 w, float2 *W) {
+    W[1] = w;
 #pragma unroll
-    for (int j = 0; j < kMaxPasses; ++j) {
-        if (j >= P.npass) break;
-        int d = (n / P.prefix[j]) % P.radix[j];
-        p += d * P.stride[j];
+    for (int k = 2; k < R; ++k) {
+        int h = 1;
+        while (2 * h <= k) h *= 2;
+        W[k] = (h == k) ? cmul(W[h / 2], W[h / 2]) : cmul(W[h], W[k - h]);
     }
-    return p;
-}
-// slot -> natural index
-__device__ __forceinline__ int index_of_slot(const PassArgs &P, int p) {
-    int n = 0;
-#pragma unroll
-    for (int j = 0; j < kMaxPasses; ++j) {
-        if (j >= P.npass) break;
-        int d = (p / P.stride[j]) % P.radix[j];
-        n += d * P.prefix[j];
-    }
-    return n;
 }
 
-// One pass j over all groups.  DIT: twiddle then DFT; DIF: DFT then twiddle.
-// Group g: b = g / s, o = g % s, slots b*(R*s) + o + i*s.
-// load(i, slot) -> float2, store(k, slot, value).
-template <int R, bool INV, bool DIT, class Load, class Store>
-__device__ __forceinline__ void pass_r(const PassArgs &P, int j, Load load, Store store) {
-    const int s = P.stride[j];
-    const int B = R * s;
-    const int tstep = P.L / B;  // W_B^e = W_L^{e * tstep}
-    const int ngroups = P.L / R;
-    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
-        const int b = g / s, o = g - b * s;
-        const int base = b * B + o;
+// A middle pass j (shared -> shared).  Group g: b = g / s, o = g % s, slots
+// b*R*s + o + i*s.  DIT: twiddle W_{Rs}^{o i} then DFT; DIF: DFT then W^{o k}.
+template <int R, bool INV, bool DIT>
+__device__ __forceinline__ void mid_pass_r(const PassArgs &P, int j, float2 *sm,
+                                           const float2 *tws) {
+    const int s = P.stride[j], B = R * s, tstep = P.L / B, ng = P.L / R;
+    const uint32_t ms = P.mag_stride[j];
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int b = (int)udiv(g, ms), o = g - b * s, base = b * B + o;
         float2 x[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) x[i] = load(i, base + i * s);
-        if (DIT) {
+        for (int i = 0; i < R; ++i) x[i] = sm[phys(base + i * s)];
+        if (!DIT) Dft<R, INV>::run(x);
+        if (o) {
+            float2 W[R];
+            tw_powers<R>(tw_base(tws, o * tstep), W);
 #pragma unroll
-            for (int i = 1; i < R; ++i)
-                if (o) x[i] = twmul<INV>(x[i], twiddle(P, o * i * tstep));
-            Dft<R, INV>::run(x);
-        } else {
-            Dft<R, INV>::run(x);
+            for (int i = 1; i < R; ++i) x[i] = twmul<INV>(x[i], W[i]);
+        }
+        if (DIT) Dft<R, INV>::run(x);
 #pragma unroll
-            for (int k = 1; k < R; ++k)
-                if (o) x[k] = twmul<INV>(x[k], twiddle(P, o * k * tstep));
+        for (int k = 0; k < R; ++k) sm[phys(base + k * s)] = x[k];
+    }
+}
+
+// pass 0 of the inverse DIF, reading the natural-order row from global memory
+template <int R>
+__device__ __forceinline__ void dif_first_r(const PassArgs &P, const float2 *__restrict__ irow,
+                                            float2 *sm, const float2 *tws) {
+    const int s = P.stride[0];
+    for (int o = threadIdx.x; o < s; o += blockDim.x) {
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = irow[o + i * s];
+        Dft<R, true>::run(x);
+        if (o) {
+            float2 W[R];
+            tw_powers<R>(tw_base(tws, o), W);
+#pragma unroll
+            for (int k = 1; k < R; ++k) x[k] = twmul<true>(x[k], W[k]);
         }
 #pragma unroll
-        for (int k = 0; k < R; ++k) store(k, base + k * s, x[k]);
+        for (int k = 0; k < R; ++k) sm[phys(o + k * s)] = x[k];
     }
 }
 
-template <bool INV, bool DIT, class Load, class Store>
-__device__ void pass_any(const PassArgs &P, int j, Load load, Store store) {
-    switch (P.radix[j]) {
-        case 2: pass_r<2, INV, DIT>(P, j, load, store); break;
-        case 3: pass_r<3, INV, DIT>(P, j, load, store); break;
-        case 4: pass_r<4, INV, DIT>(P, j, load, store); break;
-        case 5: pass_r<5, INV, DIT>(P, j, load, store); break;
-        case 6: pass_r<6, INV, DIT>(P, j, load, store); break;
-        case 8: pass_r<8, INV, DIT>(P, j, load, store); break;
-        case 9: pass_r<9, INV, DIT>(P, j, load, store); break;
-        case 10: pass_r<10, INV, DIT>(P, j, load, store); break;
-        case 12: pass_r<12, INV, DIT>(P, j, load, store); break;
-        case 15: pass_r<15, INV, DIT>(P, j, load, store); break;
-        case 16: pass_r<16, INV, DIT>(P, j, load, store); break;
-        default: break;
+// last pass (P-1, stride 1) of the inverse DIF fused with the chirp (slot
+// order), a copy of the result to scratch, and the first forward DIT pass
+template <int R>
+__device__ __forceinline__ void fused_mid_r(const PassArgs &P, float2 *sm,
+                                            const float2 *__restrict__ chirp_slot,
+                                            float2 *__restrict__ scr) {
+    const int ng = P.L / R;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int base = g * R;
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = sm[phys(base + i)];
+        Dft<R, true>::run(x);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            x[k] = cmul(x[k], __ldg(chirp_slot + base + k));
+            scr[base + k] = x[k];
+        }
+        Dft<R, false>::run(x);
+#pragma unroll
+        for (int k = 0; k < R; ++k) sm[phys(base + k)] = x[k];
     }
 }
 
-// forward DIT over passes npass-1 .. 1 in shared memory; pass 0 writes
-// out[(2k + a)] * (-1)^k for natural frequency k
-__device__ __forceinline__ void dit_forward_to_global(const PassArgs &P, float2 *sm, float2 *orow,
-                                                      int a) {
-    auto lsm = [&](int, int p) { return sm[phys(p)]; };
-    auto ssm = [&](int, int p, float2 v) { sm[phys(p)] = v; };
-    for (int j = P.npass - 1; j >= 1; --j) {
-        pass_any<false, true>(P, j, lsm, ssm);
+// the odd half: reload the chirped samples, modulate, first forward DIT pass
+template <int R>
+__device__ __forceinline__ void odd_first_r(const PassArgs &P, float2 *sm,
+                                            const float2 *__restrict__ scr) {
+    const int ng = P.L / R;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int base = g * R;
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = cmul(scr[base + i], __ldg(P.mod1_slot + base + i));
+        Dft<R, false>::run(x);
+#pragma unroll
+        for (int k = 0; k < R; ++k) sm[phys(base + k)] = x[k];
+    }
+}
+
+// padded forward pass, first step: natural-order loads (thread <-> n_b), the
+// deapodisation and modulation, the first DIT pass, stored at slot(n_b) + k
+template <int R>
+__device__ __forceinline__ void pad_first_r(const PassArgs &P, const float2 *__restrict__ irow,
+                                            float2 *sm, int a) {
+    const int nb = P.L / R;
+    for (int n = threadIdx.x; n < nb; n += blockDim.x) {
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int m = n + i * nb;
+            float2 v = cscale(irow[m], __ldg(P.pad_pre + m));
+            x[i] = a ? cmul(v, __ldg(P.mod1 + m)) : v;
+        }
+        Dft<R, false>::run(x);
+        // slot of n: digits in radices 0..P-2
+        uint32_t q = n;
+        int base = 0;
+        for (int j = 0; j < P.npass - 1; ++j) {
+            uint32_t q2 = udiv(q, P.mag_radix[j]);
+            base += (int)(q - q2 * P.radix[j]) * P.stride[j];
+            q = q2;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) sm[phys(base + k)] = x[k];
+    }
+}
+
+// pass 0 of the forward DIT: shared -> global, out[2k + a] = (-1)^k X[k]
+template <int R>
+__device__ __forceinline__ void dit_last_r(const PassArgs &P, const float2 *sm, const float2 *tws,
+                                           float2 *__restrict__ orow, int a) {
+    const int s = P.stride[0];
+    for (int o = threadIdx.x; o < s; o += blockDim.x) {
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = sm[phys(o + i * s)];
+        if (o) {
+            float2 W[R];
+            tw_powers<R>(tw_base(tws, o), W);
+#pragma unroll
+            for (int i = 1; i < R; ++i) x[i] = twmul<false>(x[i], W[i]);
+        }
+        Dft<R, false>::run(x);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int f = o + k * s;
+            float2 v = x[k];
+            if (f & 1) v = make_float2(-v.x, -v.y);
+            orow[2 * f + a] = v;
+        }
+    }
+}
+
+#define NUFDS_RADIX_SWITCH(R_, CALL)                   \
+    switch (R_) {                                      \
+        case 2: CALL(2); break;                        \
+        case 3: CALL(3); break;                        \
+        case 4: CALL(4); break;                        \
+        case 5: CALL(5); break;                        \
+        case 6: CALL(6); break;                        \
+        case 8: CALL(8); break;                        \
+        case 9: CALL(9); break;                        \
+        case 10: CALL(10); break;                      \
+        case 12: CALL(12); break;                      \
+        case 15: CALL(15); break;                      \
+        case 16: CALL(16); break;                      \
+        default: break;                                \
+    }
+
+template <bool INV, bool DIT>
+__device__ void mid_pass(const PassArgs &P, int j, float2 *sm, const float2 *tws) {
+#define C_(R) mid_pass_r<R, INV, DIT>(P, j, sm, tws)
+    NUFDS_RADIX_SWITCH(P.radix[j], C_)
+#undef C_
+}
+
+__device__ void forward_tail(const PassArgs &P, float2 *sm, const float2 *tws, float2 *orow,
+                             int a) {
+    for (int j = P.npass - 2; j >= 1; --j) {
+        mid_pass<false, true>(P, j, sm, tws);
         __syncthreads();
     }
-    auto sgl = [&](int, int k, float2 v) {
-        if (k & 1) v = make_float2(-v.x, -v.y);
-        orow[2 * k + a] = v;
-    };
-    pass_any<false, true>(P, 0, lsm, sgl);
+#define C_(R) dit_last_r<R>(P, sm, tws, orow, a)
+    NUFDS_RADIX_SWITCH(P.radix[0], C_)
+#undef C_
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_rows_pad2(PassArgs P, const float2 *__restrict__ in,
-                                                    long in_ld, float2 *__restrict__ out,
-                                                    long out_ld, int rows) {
+// dynamic shared memory: padded row, then the twiddle tables
+__device__ __forceinline__ float2 *load_tw(const PassArgs &P, float2 *sm) {
+    float2 *tws = sm + phys(P.L) + 1;
+    for (int i = threadIdx.x; i < 64 + P.ncoarse; i += blockDim.x) tws[i] = P.tw[i];
+    __syncthreads();
+    return tws;
+}
+
+__global__ void __launch_bounds__(512) k_rows_pad2(PassArgs P, const float2 *__restrict__ in,
+                                                   long in_ld, float2 *__restrict__ out,
+                                                   long out_ld, int rows) {
     extern __shared__ float2 sm[];
-    const int L = P.L;
+    const float2 *tws = load_tw(P, sm);
+    const int RL = P.radix[P.npass - 1];
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         const float2 *irow = in + (long)r * in_ld;
         float2 *orow = out + (long)r * out_ld;
         for (int a = 0; a < 2; ++a) {
-            for (int n = threadIdx.x; n < L; n += blockDim.x) {
-                float2 v = cscale(irow[n], __ldg(P.pad_pre + n));
-                if (a) v = cmul(v, __ldg(P.mod1 + n));
-                sm[phys(slot_of_index(P, n))] = v;
-            }
+#define C_(R) pad_first_r<R>(P, irow, sm, a)
+            NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
             __syncthreads();
-            dit_forward_to_global(P, sm, orow, a);
+            forward_tail(P, sm, tws, orow, a);
         }
     }
 }
 
-__global__ void __launch_bounds__(1024) k_rows_view(PassArgs P, const float2 *__restrict__ in,
-                                                    long in_ld, const float2 *__restrict__ chirp,
-                                                    float2 *__restrict__ out, long out_ld, int rows,
-                                                    float2 *__restrict__ scratch) {
+__global__ void __launch_bounds__(512) k_rows_view(PassArgs P, const float2 *__restrict__ in,
+                                                   long in_ld,
+                                                   const float2 *__restrict__ chirp_slot,
+                                                   float2 *__restrict__ out, long out_ld,
+                                                   int rows, float2 *__restrict__ scratch) {
     extern __shared__ float2 sm[];
-    const int L = P.L;
-    float2 *scr = scratch + (long)blockIdx.x * L;
-    auto lsm = [&](int, int p) { return sm[phys(p)]; };
-    auto ssm = [&](int, int p, float2 v) { sm[phys(p)] = v; };
+    const float2 *tws = load_tw(P, sm);
+    float2 *scr = scratch + (long)blockIdx.x * P.L;
+    const int RL = P.radix[P.npass - 1];
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         const float2 *irow = in + (long)r * in_ld;
         float2 *orow = out + (long)r * out_ld;
-        // inverse DFT (DIF): natural -> digit-reversed
-        auto lgl = [&](int, int p) { return irow[p]; };
-        pass_any<true, false>(P, 0, lgl, ssm);
+        // inverse DFT (DIF): natural -> slot order
+#define C_(R) dif_first_r<R>(P, irow, sm, tws)
+        NUFDS_RADIX_SWITCH(P.radix[0], C_)
+#undef C_
         __syncthreads();
-        for (int j = 1; j < P.npass; ++j) {
-            pass_any<true, false>(P, j, lsm, ssm);
+        for (int j = 1; j < P.npass - 1; ++j) {
+            mid_pass<true, false>(P, j, sm, tws);
             __syncthreads();
         }
-        // chirp (with deapodisation and 1/L); keep a copy for the odd half
-        for (int p = threadIdx.x; p < L; p += blockDim.x) {
-            float2 v = cmul(sm[phys(p)], __ldg(chirp + index_of_slot(P, p)));
-            sm[phys(p)] = v;
-            scr[p] = v;
-        }
+        // last inverse pass + chirp + first forward pass
+#define C_(R) fused_mid_r<R>(P, sm, chirp_slot, scr)
+        NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
         __syncthreads();
-        dit_forward_to_global(P, sm, orow, 0);
-        for (int p = threadIdx.x; p < L; p += blockDim.x)
-            sm[phys(p)] = cmul(scr[p], __ldg(P.mod1 + index_of_slot(P, p)));
+        forward_tail(P, sm, tws, orow, 0);
+#define C_(R) odd_first_r<R>(P, sm, scr)
+        NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
         __syncthreads();
-        dit_forward_to_global(P, sm, orow, 1);
+        forward_tail(P, sm, tws, orow, 1);
     }
 }
 
@@ -313,24 +427,114 @@ __global__ void __launch_bounds__(1024) k_rows_view(PassArgs P, const float2 *__
 // ------------------------------------------------------------------------
 static const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
 
-// fewest passes, then the largest smallest radix
-static bool factor(int L, int depth, int *out, int &best_n, int *best, int *cur) {
+static int host_phys(int p) { return p + (p >> 4) + (p >> 8); }
+
+// all multisets of radices (non-increasing) with the fewest factors
+static void factor_sets(int L, std::vector<int> &cur, std::vector<std::vector<int>> &out,
+                        int &best) {
     if (L == 1) {
-        if (depth < best_n) {
-            best_n = depth;
-            for (int i = 0; i < depth; ++i) best[i] = cur[i];
+        if ((int)cur.size() < best) {
+            best = (int)cur.size();
+            out.clear();
         }
-        return true;
+        if ((int)cur.size() == best) out.push_back(cur);
+        return;
     }
-    if (depth + 1 >= best_n || depth >= kMaxPasses) return false;
+    if ((int)cur.size() >= best || (int)cur.size() >= kMaxPasses) return;
     for (int r : kRadices) {
-        if (L % r) continue;
-        if (depth > 0 && r > cur[depth - 1]) continue;  // non-increasing: avoid permutations
-        cur[depth] = r;
-        factor(L / r, depth + 1, out, best_n, best, cur);
+        if (L % r || (!cur.empty() && r > cur.back())) continue;
+        cur.push_back(r);
+        factor_sets(L / r, cur, out, best);
+        cur.pop_back();
     }
-    (void)out;
-    return best_n <= kMaxPasses;
+}
+
+// shared-memory wavefronts of one warp access (8-byte elements, 32 banks)
+static int waves(const int *slots, int n) {
+    int cnt[32];
+    int words[32][64];
+    for (int b = 0; b < 32; ++b) cnt[b] = 0;
+    int worst = 0;
+    for (int t = 0; t < n; ++t) {
+        int ph = host_phys(slots[t]);
+        for (int w = 2 * ph; w <= 2 * ph + 1; ++w) {
+            int b = w & 31, seen = 0;
+            for (int k = 0; k < cnt[b]; ++k) seen |= words[b][k] == w;
+            if (!seen && cnt[b] < 64) words[b][cnt[b]++] = w;
+            if (cnt[b] > worst) worst = cnt[b];
+        }
+    }
+    return worst;
+}
+
+// bank-conflict cost of a radix order: middle passes and the padded-pass scatter
+static double order_cost(const std::vector<int> &rad) {
+    const int P = (int)rad.size();
+    int L = 1;
+    for (int r : rad) L *= r;
+    std::vector<int> st(P);
+    int rem = L;
+    for (int j = 0; j < P; ++j) st[j] = (rem /= rad[j]);
+    double sum = 0, mx = 0;
+    int slots[32];
+    for (int j = 1; j < P; ++j) {
+        const int R = rad[j], B = R * st[j];
+        double w = 0;
+        for (int i = 0; i < R; ++i) {
+            for (int t = 0; t < 32; ++t) slots[t] = (t / st[j]) * B + t % st[j] + i * st[j];
+            w += waves(slots, 32);
+        }
+        w /= 2.0 * R;
+        sum += w;
+        mx = std::max(mx, w);
+    }
+    const int R = rad[P - 1];
+    double w = 0;
+    for (int k = 0; k < R; ++k) {
+        for (int t = 0; t < 32; ++t) {
+            int q = t, p = 0;
+            for (int j = 0; j < P - 1; ++j) {
+                p += (q % rad[j]) * st[j];
+                q /= rad[j];
+            }
+            slots[t] = p + k;
+        }
+        w += waves(slots, 32);
+    }
+    w /= 2.0 * R;
+    return sum + w + std::max(mx, w);
+}
+
+static bool choose_radices(int L, FftPlan &p) {
+    std::vector<int> cur;
+    std::vector<std::vector<int>> sets;
+    int best = kMaxPasses + 1;
+    factor_sets(L, cur, sets, best);
+    if (sets.empty() || best < 2) return false;
+    double bc = 1e30;
+    std::vector<int> bo;
+    for (auto &m : sets) {
+        std::vector<int> perm = m;
+        std::sort(perm.begin(), perm.end());
+        do {
+            double c = order_cost(perm);
+            if (c < bc - 1e-9) {
+                bc = c;
+                bo = perm;
+            }
+        } while (std::next_permutation(perm.begin(), perm.end()));
+    }
+    p.L = L;
+    p.npass = (int)bo.size();
+    int pre = 1, rem = L;
+    for (int j = 0; j < p.npass; ++j) {
+        p.radix[j] = bo[j];
+        p.prefix[j] = pre;
+        pre *= bo[j];
+        rem /= bo[j];
+        p.stride[j] = rem;
+    }
+    return true;
 }
 
 static double psi_es(double s) {
@@ -381,15 +585,7 @@ static void es_fourier(int L, std::vector<double> &ft) {
     }
 }
 
-struct LenEntry {
-    FftPlan plan;
-    float2 *dev = nullptr;  // tw_fine | tw_coarse | mod1
-    double *deapod = nullptr;
-    float *pad_pre = nullptr;
-};
-
 static std::mutex g_mu;
-static std::map<std::pair<int, int>, LenEntry *> g_cache;  // (device, L)
 static std::map<int, bool> g_const_ready;
 
 static int init_constants() {
@@ -408,6 +604,66 @@ static int init_constants() {
     return 0;
 }
 
+static int slot_to_index(const FftPlan &p, int slot) {
+    int n = 0;
+    for (int j = 0; j < p.npass; ++j) n += ((slot / p.stride[j]) % p.radix[j]) * p.prefix[j];
+    return n;
+}
+
+// Plan of length L and its host tables:
+//   f2: fine[64] | coarse[ncoarse] | mod1[L] | mod1_slot[L]; dea[L]; pad[L]
+static int plan_host(int L, FftPlan &p, std::vector<float2> &f2, std::vector<double> &dea,
+                     std::vector<float> &pad) {
+    if (L < 64 || (L % 4) || !choose_radices(L, p)) return -3;
+    int t = (L / 16 + 31) / 32 * 32;
+    p.threads = t < 64 ? 64 : (t > 512 ? 512 : t);
+    p.ncoarse = (L + 63) / 64;
+    p.smem_bytes = sizeof(float2) * (size_t)(host_phys(L) + 1 + 64 + p.ncoarse);
+    if (p.smem_bytes > 227 * 1024) return -3;
+    f2.assign(64 + p.ncoarse + 2 * (size_t)L, make_float2(0.f, 0.f));
+    for (int j = 0; j < 64; ++j) {
+        double a = -2.0 * M_PI * j / L;
+        f2[j] = make_float2((float)cos(a), (float)sin(a));
+    }
+    for (int i = 0; i < p.ncoarse; ++i) {
+        double a = -2.0 * M_PI * (double)(64L * i % L) / L;
+        f2[64 + i] = make_float2((float)cos(a), (float)sin(a));
+    }
+    float2 *mod1 = f2.data() + 64 + p.ncoarse, *mod1s = mod1 + L;
+    for (int n = 0; n < L; ++n) {
+        double a = -M_PI * (n - L / 2) / (double)L;
+        mod1[n] = make_float2((float)cos(a), (float)sin(a));
+    }
+    for (int q = 0; q < L; ++q) mod1s[q] = mod1[slot_to_index(p, q)];
+    std::vector<double> ft;
+    es_fourier(L, ft);
+    dea.resize(L);
+    pad.resize(L);
+    for (int n = 0; n < L; ++n) {
+        dea[n] = 1.0 / ft[n];
+        pad[n] = (float)((n & 1) ? -dea[n] : dea[n]);
+    }
+    return 0;
+}
+
+static void plan_point(FftPlan &p, const float2 *tw, const double *dea, const float *pad) {
+    p.tw = tw;
+    p.mod1 = tw + 64 + p.ncoarse;
+    p.mod1_slot = p.mod1 + p.L;
+    p.deapod = dea;
+    p.pad_pre = pad;
+}
+
+struct LenEntry {
+    FftPlan plan;
+    float2 *dev = nullptr;
+    double *deapod = nullptr;
+    float *pad_pre = nullptr;
+};
+static std::map<std::pair<int, int>, LenEntry *> g_cache;  // (device, L)
+
+static void set_smem_attrs(size_t bytes);
+
 int fft_plan_get(int L, const FftPlan **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     int rc = init_constants();
@@ -420,160 +676,88 @@ int fft_plan_get(int L, const FftPlan **out) {
         *out = &it->second->plan;
         return 0;
     }
-    int best[kMaxPasses], cur[kMaxPasses], best_n = kMaxPasses + 1;
-    factor(L, 0, nullptr, best_n, best, cur);
-    if (best_n > kMaxPasses || L < 16 || (L % 4)) return -3;
     LenEntry *e = new LenEntry();
-    FftPlan &p = e->plan;
-    p.L = L;
-    p.npass = best_n;
-    int pre = 1, rem = L;
-    for (int j = 0; j < best_n; ++j) {
-        p.radix[j] = best[j];
-        p.prefix[j] = pre;
-        pre *= best[j];
-        rem /= best[j];
-        p.stride[j] = rem;
+    std::vector<float2> f2;
+    std::vector<double> dea;
+    std::vector<float> pad;
+    if ((rc = plan_host(L, e->plan, f2, dea, pad))) {
+        delete e;
+        return rc;
     }
-    int t = (L / 16 + 31) / 32 * 32;
-    p.threads = t < 64 ? 64 : (t > 1024 ? 1024 : t);
-    p.smem_bytes = sizeof(float2) * (size_t)(L + L / 16 + 1);
-    // tables
-    int ncoarse = (L + 63) / 64;
-    std::vector<float2> h(64 + ncoarse + L);
-    for (int j = 0; j < 64; ++j) {
-        double a = -2.0 * M_PI * j / L;
-        h[j] = make_float2((float)cos(a), (float)sin(a));
-    }
-    for (int i = 0; i < ncoarse; ++i) {
-        double a = -2.0 * M_PI * (double)(64L * i % L) / L;
-        h[64 + i] = make_float2((float)cos(a), (float)sin(a));
-    }
-    for (int n = 0; n < L; ++n) {
-        double a = -M_PI * (n - L / 2) / (double)L;
-        h[64 + ncoarse + n] = make_float2((float)cos(a), (float)sin(a));
-    }
-    std::vector<double> ft;
-    es_fourier(L, ft);
-    std::vector<double> dea(L);
-    std::vector<float> pp(L);
-    for (int n = 0; n < L; ++n) {
-        dea[n] = 1.0 / ft[n];
-        pp[n] = (float)((n & 1) ? -dea[n] : dea[n]);
-    }
-    if (cudaMalloc(&e->dev, sizeof(float2) * h.size()) != cudaSuccess ||
+    if (cudaMalloc(&e->dev, sizeof(float2) * f2.size()) != cudaSuccess ||
         cudaMalloc(&e->deapod, sizeof(double) * L) != cudaSuccess ||
         cudaMalloc(&e->pad_pre, sizeof(float) * L) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(e->dev);
+        cudaFree(e->deapod);
         delete e;
         return -2;
     }
-    cudaMemcpy(e->dev, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(e->dev, f2.data(), sizeof(float2) * f2.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(e->deapod, dea.data(), sizeof(double) * L, cudaMemcpyHostToDevice);
-    cudaMemcpy(e->pad_pre, pp.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
-    p.tw_fine = e->dev;
-    p.tw_coarse = e->dev + 64;
-    p.mod1 = e->dev + 64 + ncoarse;
-    p.deapod = e->deapod;
-    p.pad_pre = e->pad_pre;
-    if (p.smem_bytes > 48 * 1024) {
-        cudaFuncSetAttribute(k_rows_pad2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-        cudaFuncSetAttribute(k_rows_view, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-    }
-    if (p.smem_bytes > 227 * 1024) {
-        delete e;
-        return -3;
-    }
+    cudaMemcpy(e->pad_pre, pad.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
+    plan_point(e->plan, e->dev, e->deapod, e->pad_pre);
+    set_smem_attrs(e->plan.smem_bytes);
     g_cache[key] = e;
-    *out = &p;
+    *out = &e->plan;
     return 0;
 }
 
-// Plan and tables of length L written into caller-provided device memory
-// (no allocation): d_tw holds 64 + ceil(L/64) + L float2, d_deapod L doubles,
-// d_pad L floats.  Tables are computed on the host in FP64 and copied on st.
+// Plan and tables of length L written into caller-provided device memory (no
+// allocation): d_tw holds fft_tw_count(L) float2, d_deapod L doubles, d_pad L
+// floats.  Tables are computed on the host in FP64 and copied on st.
 int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pad,
                   cudaStream_t st) {
+    std::vector<float2> f2;
+    std::vector<double> dea;
+    std::vector<float> pad;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         int rc = init_constants();
         if (rc) return rc;
+        *p = FftPlan();
+        if ((rc = plan_host(L, *p, f2, dea, pad))) return rc;
     }
-    int best[kMaxPasses], cur[kMaxPasses], best_n = kMaxPasses + 1;
-    factor(L, 0, nullptr, best_n, best, cur);
-    if (best_n > kMaxPasses || L < 16 || (L % 4)) return -3;
-    *p = FftPlan();
-    p->L = L;
-    p->npass = best_n;
-    int pre = 1, rem = L;
-    for (int j = 0; j < best_n; ++j) {
-        p->radix[j] = best[j];
-        p->prefix[j] = pre;
-        pre *= best[j];
-        rem /= best[j];
-        p->stride[j] = rem;
-    }
-    int t = (L / 16 + 31) / 32 * 32;
-    p->threads = t < 64 ? 64 : (t > 1024 ? 1024 : t);
-    p->smem_bytes = sizeof(float2) * (size_t)(L + L / 16 + 1);
     if (p->smem_bytes > 48 * 1024) return -3;
-    int ncoarse = (L + 63) / 64;
-    std::vector<float2> h(64 + ncoarse + L);
-    for (int j = 0; j < 64; ++j) {
-        double a = -2.0 * M_PI * j / L;
-        h[j] = make_float2((float)cos(a), (float)sin(a));
-    }
-    for (int i = 0; i < ncoarse; ++i) {
-        double a = -2.0 * M_PI * (double)(64L * i % L) / L;
-        h[64 + i] = make_float2((float)cos(a), (float)sin(a));
-    }
-    for (int n = 0; n < L; ++n) {
-        double a = -M_PI * (n - L / 2) / (double)L;
-        h[64 + ncoarse + n] = make_float2((float)cos(a), (float)sin(a));
-    }
-    std::vector<double> ft;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        es_fourier(L, ft);
-    }
-    std::vector<double> dea(L);
-    std::vector<float> pp(L);
-    for (int n = 0; n < L; ++n) {
-        dea[n] = 1.0 / ft[n];
-        pp[n] = (float)((n & 1) ? -dea[n] : dea[n]);
-    }
-    if (cudaMemcpyAsync(d_tw, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice, st) !=
+    if (cudaMemcpyAsync(d_tw, f2.data(), sizeof(float2) * f2.size(), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(d_deapod, dea.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
-        cudaMemcpyAsync(d_pad, pp.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st) !=
+        cudaMemcpyAsync(d_pad, pad.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st) !=
             cudaSuccess)
         return -4;
     // pageable sources: keep them alive until the copies have been consumed
     if (cudaStreamSynchronize(st) != cudaSuccess) return -4;
-    p->tw_fine = d_tw;
-    p->tw_coarse = d_tw + 64;
-    p->mod1 = d_tw + 64 + ncoarse;
-    p->deapod = d_deapod;
-    p->pad_pre = d_pad;
+    plan_point(*p, d_tw, d_deapod, d_pad);
     return 0;
 }
 
+size_t fft_tw_count(int L) { return 64 + (size_t)(L + 63) / 64 + 2 * (size_t)L; }
+
 static PassArgs pass_args(const FftPlan &p) {
     PassArgs a;
+    memset(&a, 0, sizeof a);
     a.L = p.L;
     a.npass = p.npass;
-    for (int j = 0; j < kMaxPasses; ++j) {
+    a.ncoarse = p.ncoarse;
+    for (int j = 0; j < p.npass; ++j) {
         a.radix[j] = p.radix[j];
         a.stride[j] = p.stride[j];
-        a.prefix[j] = p.prefix[j];
+        a.mag_stride[j] = p.stride[j] == 1 ? 0u : (uint32_t)(((1ull << 32) + p.stride[j] - 1) / p.stride[j]);
+        a.mag_radix[j] = (uint32_t)(((1ull << 32) + p.radix[j] - 1) / p.radix[j]);
     }
-    a.tw_fine = p.tw_fine;
-    a.tw_coarse = p.tw_coarse;
+    a.tw = p.tw;
     a.mod1 = p.mod1;
+    a.mod1_slot = p.mod1_slot;
     a.pad_pre = p.pad_pre;
     return a;
+}
+
+static void set_smem_attrs(size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaFuncSetAttribute(k_rows_pad2, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_rows_view, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    }
 }
 
 static int grid_for(const void *fn, const FftPlan &p, int rows) {

@@ -37,14 +37,24 @@ struct FftPlan {
     int stride[kMaxPasses] = {};   // s_j = L / (r_1 ... r_j)
     int prefix[kMaxPasses] = {};   // r_1 ... r_{j-1}
     int threads = 0;
+    int ncoarse = 0;                   // ceil(L / 64)
     size_t smem_bytes = 0;
-    // device tables (owned by the length cache)
-    const float2 *tw_fine = nullptr;   // W_L^j, j < 64
-    const float2 *tw_coarse = nullptr; // W_L^{64 i}, i < ceil(L/64)
-    const float2 *mod1 = nullptr;      // e^{-i pi (n - L/2)/L}
+    // device tables (owned by the length cache, or caller memory)
+    const float2 *tw = nullptr;        // W_L^j (j < 64) | W_L^{64 i} (i < ncoarse)
+    const float2 *mod1 = nullptr;      // e^{-i pi (n - L/2)/L}, natural order
+    const float2 *mod1_slot = nullptr; // the same in digit-reversed slot order
     const double *deapod = nullptr;    // 1 / psi_hat(n - L/2)
     const float *pad_pre = nullptr;    // (-1)^n / psi_hat(n - L/2)
 };
+
+// Natural index of a digit-reversed slot of plan p (host and device).
+__host__ __device__ inline int fft_index_of_slot(const FftPlan &p, int slot) {
+    int n = 0;
+    for (int j = 0; j < p.npass; ++j) n += ((slot / p.stride[j]) % p.radix[j]) * p.prefix[j];
+    return n;
+}
+// float2 count of the twiddle/modulation table of length L
+size_t fft_tw_count(int L);
 
 // Build (or fetch from the per-device cache) the plan and tables of length L.
 int fft_plan_get(int L, const FftPlan **out);
@@ -88,9 +98,10 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
                        double px, double py, int ox, int oy, short2 *base, float2 *frac,
                        cudaStream_t st);
-// chirp[n] = e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) N pitch / L
-int launch_chirp_table(const double *deapod, int L, double window_m, double lam, double z,
-                       float2 *chirp, cudaStream_t st);
+// chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L at n = natural index of the
+// slot (digit-reversed order of plan fp), x_n = (n - L/2) window / L
+int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,
+                       cudaStream_t st);
 // Output chirp pieces: E[b - b0] = e^{i kappa b^2 / 4} for b in [b0, b0 + nb)
 int launch_outchirp_table(double kappa, long b0, int nb, float2 *E, cudaStream_t st);
 

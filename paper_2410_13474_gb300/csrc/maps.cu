@@ -182,18 +182,21 @@ __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z
     frac[idx] = f;
 }
 
-// chirp[n] = e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) window / L
-__global__ void k_chirp_table(const double *deapod, int L, double window, double lam, double z,
-                              float2 *chirp) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L) return;
+// chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) window / L,
+// n the natural index of the slot in the digit-reversed order of the row FFT
+__global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, float2 *chirp) {
+    const int L = fp.L;
+    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= L) return;
+    const int n = fft_index_of_slot(fp, slot);
+    const double *deapod = fp.deapod;
     double x = (n - L / 2) * (window / L);
     double ph = M_PI * x * x / (lam * z);
     ph -= 2.0 * M_PI * rint(ph / (2.0 * M_PI));
     double s, c;
     sincos(ph, &s, &c);
     double a = deapod[n] / L;
-    chirp[n] = make_float2((float)(c * a), (float)(s * a));
+    chirp[slot] = make_float2((float)(c * a), (float)(s * a));
 }
 
 __global__ void k_outchirp_table(double kappa, long b0, int nb, float2 *E) {
@@ -228,9 +231,9 @@ int launch_remap_table(double lam, double pitch, int nx, int ny, double z, doubl
     return check_launch();
 }
 
-int launch_chirp_table(const double *deapod, int L, double window_m, double lam, double z,
-                       float2 *chirp, cudaStream_t st) {
-    k_chirp_table<<<(L + 255) / 256, 256, 0, st>>>(deapod, L, window_m, lam, z, chirp);
+int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,
+                       cudaStream_t st) {
+    k_chirp_table<<<(fp.L + 255) / 256, 256, 0, st>>>(fp, window_m, lam, z, chirp);
     count_launch();
     return check_launch();
 }
