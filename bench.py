@@ -309,6 +309,32 @@ def run_ours(args, w):
                     "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
             "roofline": roof, "stages": stages, "clocks": clk, "gpu_launches": int(launches),
             "init_ms": round(init_ms, 1), "input_gen_s": round(gen_s, 2)}
+    # storage-precision variants of the same step (FP32 arithmetic), with the
+    # relative L2 of their intensity against the FP32 path's
+    ref_out = out.clone()
+    variants = {}
+    for vname, prec in (("fp16_store", nf.FP16_STORE), ("bf16_store", nf.BF16_STORE)):
+        vp = nf.Plan(w.wavelength, w.pitch, n, n, precision=prec)
+        vout = vp.output_like(view)
+        vp.load(d_holo)
+        vp.reconstruct(view, vout)
+        torch.cuda.synchronize()
+        ksteps = max(3, args.steps // 4)
+        ev0.record(stream)
+        for _ in range(ksteps):
+            vp.load(d_holo)
+            vp.reconstruct(view, vout)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        vms = ev0.elapsed_time(ev1) / ksteps
+        err = float(torch.linalg.vector_norm(vout - ref_out) / torch.linalg.vector_norm(ref_out))
+        variants[vname] = {"ms_per_step": round(vms, 3),
+                           "value": round(world * pix / (vms * 1e-3) / 1e6, 2),
+                           "intensity_rel_l2_vs_fp32_path": float("%.3e" % err),
+                           "steps": ksteps}
+        vp.close()
+        del vout
+    line["precision_variants"] = variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     plan.close()

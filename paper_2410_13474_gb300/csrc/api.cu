@@ -61,8 +61,11 @@ struct nufds_plan {
     // output map on the full-view pixel lattice (z independent)
     short2 *rm_base = nullptr;
     float2 *rm_frac = nullptr;
-    // cached oversampled spectrum, [mx][my]
-    float2 *G = nullptr;
+    // cached oversampled spectrum, [mx][my], in the plan's storage precision
+    int prec = NUFDS_FP32;
+    void *G = nullptr;
+    float *sc = nullptr;   // FP16 scales (see launch_scales_load / _view)
+    double *acc = nullptr; // energies behind the FP16 scales
     bool loaded = false;
     // workspace arena
     char *ws = nullptr;
@@ -247,9 +250,9 @@ struct ViewWs {
 
 static int view_ws(const nufds_plan *P, const ViewPlan &V, const FftPlan *fpx, const FftPlan *fpy,
                    int kind, ViewWs *w) {
-    const size_t np = (size_t)V.npx * V.npy;
-    w->A = align256(sizeof(float2) * 4 * np);
-    w->B = align256(sizeof(float2) * 2 * np);
+    const size_t np = (size_t)V.npx * V.npy, eb = prec_bytes(P->prec);
+    w->A = align256(eb * 4 * np);
+    w->B = align256(eb * 2 * np);
     w->grid_y = rows_view_grid(*fpy, V.npx);
     w->grid_x = rows_view_grid(*fpx, 2 * V.npy);
     size_t sy = (size_t)w->grid_y * V.npy, sx = (size_t)w->grid_x * V.npx;
@@ -283,26 +286,55 @@ static int ensure_ws(nufds_plan *P, size_t need) {
     return NUFDS_OK;
 }
 
+// max over f of the kernel's tap sum, squared: bound of a 2-D gather's gain
+static double kernel_gain2() {
+    double best = 0;
+    for (int t = 0; t <= 1000; ++t) {
+        double f = t / 1000.0, s = 0;
+        for (int i = 0; i < kW; ++i) {
+            double d = f + (kW / 2 - 1 - i), u = 2.0 * d / kW;
+            if (fabs(u) < 1.0) s += exp(kBeta * (sqrt(1.0 - u * u) - 1.0));
+        }
+        best = fmax(best, s);
+    }
+    return best * best;
+}
+
+static const float *scale_ptr(const nufds_plan *P, int k) {
+    return P->prec == NUFDS_FP16_STORE ? P->sc + k : nullptr;
+}
+
 static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
-    const size_t half = align256(sizeof(float2) * 2 * (size_t)P->nx * P->ny);
+    const size_t eb = prec_bytes(P->prec);
+    const size_t half = align256(eb * 2 * (size_t)P->nx * P->ny);
     int rc = ensure_ws(P, 2 * half);
     if (rc) return rc;
-    float2 *A = (float2 *)P->ws, *Bf = (float2 *)(P->ws + half);
+    void *A = P->ws, *Bf = P->ws + half;
     const float2 *H = (const float2 *)d_holo;
-    const double n2 = (double)P->nx * P->ny;
+    const double n2 = (double)P->nx * P->ny, q = eb / 8.0;
+    if (P->prec == NUFDS_FP16_STORE) {
+        static const double k2 = kernel_gain2();
+        if ((rc = stage(P, ST_TABLES, 8.0 * n2, st, [&] {
+                 int r = launch_norms(H, P->nx, P->ny, P->fx->deapod, P->fy->deapod, P->acc, st);
+                 return r ? r : launch_scales_load(P->sc, P->acc, P->nx, P->ny, k2, st);
+             })))
+            return rc;
+    }
     // along x: rows of H (ny rows of nx) -> A (ny x 2nx)
-    if ((rc = stage(P, ST_PAD_ROWS_X, 24.0 * n2, st, [&] {
-             return launch_rows_pad2(*P->fx, H, P->nx, A, 2 * P->nx, P->ny, st);
+    if ((rc = stage(P, ST_PAD_ROWS_X, (8.0 + 16.0 * q) * n2, st, [&] {
+             return launch_rows_pad2(*P->fx, H, PREC_F32, P->nx, A, P->prec, 2 * P->nx, P->ny,
+                                     nullptr, scale_ptr(P, 0), st);
          })))
         return rc;
     // A (ny x 2nx) -> Bf (2nx x ny)
-    if ((rc = stage(P, ST_PAD_TRANSPOSE, 32.0 * n2, st, [&] {
-             return launch_transpose(A, 2 * P->nx, Bf, P->ny, P->ny, 2 * P->nx, st);
+    if ((rc = stage(P, ST_PAD_TRANSPOSE, 32.0 * q * n2, st, [&] {
+             return launch_transpose(A, 2 * P->nx, Bf, P->ny, P->ny, 2 * P->nx, P->prec, st);
          })))
         return rc;
     // along y: rows of Bf (2nx rows of ny) -> G (2nx x 2ny)
-    if ((rc = stage(P, ST_PAD_ROWS_Y, 48.0 * n2, st, [&] {
-             return launch_rows_pad2(*P->fy, Bf, P->ny, P->G, 2 * P->ny, 2 * P->nx, st);
+    if ((rc = stage(P, ST_PAD_ROWS_Y, 48.0 * q * n2, st, [&] {
+             return launch_rows_pad2(*P->fy, Bf, P->prec, P->ny, P->G, P->prec, 2 * P->ny,
+                                     2 * P->nx, scale_ptr(P, 0), scale_ptr(P, 1), st);
          })))
         return rc;
     P->loaded = true;
@@ -327,9 +359,9 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     view_ws(P, V, fpx, fpy, v->out_kind, &W);
     if ((rc = ensure_ws(P, W.total))) return rc;
     char *p = P->ws;
-    float2 *A = (float2 *)p;
+    void *A = p;
     p += W.A;
-    float2 *Bf = (float2 *)p;
+    void *Bf = p;
     p += W.B;
     float2 *scr = (float2 *)p;
     p += W.scr;
@@ -391,28 +423,41 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     sa.npx = V.npx;
     sa.npy = V.npy;
     sa.S = Bf;
-    const double np2 = (double)V.npx * V.npy;
+    sa.prec = P->prec;
+    sa.sc_g = scale_ptr(P, 1);
+    sa.sc_s = scale_ptr(P, 2);
+    sa.energy = P->prec == NUFDS_FP16_STORE ? P->acc + 2 : nullptr;
+    const double np2 = (double)V.npx * V.npy, q = prec_bytes(P->prec) / 8.0;
     const double nbx = (double)(V.khi_x - V.klo_x + 1), nby = (double)(V.khi_y - V.klo_y + 1);
+    if (P->prec == NUFDS_FP16_STORE &&
+        cudaMemsetAsync(P->acc + 2, 0, sizeof(double), st) != cudaSuccess)
+        return NUFDS_ECUDA;
     // algorithmic bytes of the gather: table entries of the band, the part of
     // G the band pulls back to (in proportion to the full band), S written
     const double g_frac = (nbx * nby) / ((double)P->pb_nkx * P->pb_nky);
-    const double st_bytes = 12.0 * nbx * nby + 32.0 * P->nx * P->ny * g_frac + 8.0 * np2;
+    const double st_bytes = 12.0 * nbx * nby + 32.0 * q * P->nx * P->ny * g_frac + 8.0 * q * np2;
     if ((rc = stage(P, ST_STRETCH, st_bytes, st, [&] { return launch_stretch(sa, st); })))
         return rc;
+    if (P->prec == NUFDS_FP16_STORE &&
+        (rc = stage(P, ST_TABLES, 0.0, st, [&] {
+             return launch_scales_view(P->sc, P->acc, fpx->dmax, fpy->dmax, st);
+         })))
+        return rc;
     // steps two/three along y: S_T rows (npx of npy) -> A (npx x 2npy)
-    if ((rc = stage(P, ST_VIEW_ROWS_Y, 24.0 * np2, st, [&] {
-             return launch_rows_view(*fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y, st);
+    if ((rc = stage(P, ST_VIEW_ROWS_Y, 24.0 * q * np2, st, [&] {
+             return launch_rows_view(*fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y,
+                                     P->prec, scale_ptr(P, 2), scale_ptr(P, 3), st);
          })))
         return rc;
     // A (npx x 2npy) -> Bf (2npy x npx)
-    if ((rc = stage(P, ST_VIEW_TRANSPOSE, 32.0 * np2, st, [&] {
-             return launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, st);
+    if ((rc = stage(P, ST_VIEW_TRANSPOSE, 32.0 * q * np2, st, [&] {
+             return launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, P->prec, st);
          })))
         return rc;
     // along x: Bf rows (2npy of npx) -> A = Q (2npy x 2npx)
-    if ((rc = stage(P, ST_VIEW_ROWS_X, 48.0 * np2, st, [&] {
+    if ((rc = stage(P, ST_VIEW_ROWS_X, 48.0 * q * np2, st, [&] {
              return launch_rows_view(*fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr,
-                                     W.grid_x, st);
+                                     W.grid_x, P->prec, scale_ptr(P, 4), scale_ptr(P, 5), st);
          })))
         return rc;
     // step five: remap
@@ -437,8 +482,10 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ra.kappa_x = (float)kx;
     ra.kappa_y = (float)ky;
     ra.out = d_out;
+    ra.prec = P->prec;
+    ra.sc_q = scale_ptr(P, 5);
     // Q region the view maps into, its table, the output
-    const double rm_bytes = 32.0 * nbx * nby + 12.0 * V.ox * V.oy +
+    const double rm_bytes = 32.0 * q * nbx * nby + 12.0 * V.ox * V.oy +
                             (v->out_kind == NUFDS_OUT_FIELD_C64 ? 8.0 : 4.0) * V.ox * V.oy;
     return stage(P, ST_REMAP, rm_bytes, st, [&] { return launch_remap(ra, st); });
 }
@@ -450,6 +497,7 @@ static void free_plan(nufds_plan *P) {
     cudaFree(P->rm_base);
     cudaFree(P->rm_frac);
     cudaFree(P->G);
+    cudaFree(P->sc);
     cudaFree(P->ws);
     for (cudaEvent_t e : P->events) cudaEventDestroy(e);
     delete P;
@@ -492,7 +540,9 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
         !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->reserved != 0 || prm->nx <= 0 ||
         prm->ny <= 0 || prm->nx % 4 || prm->ny % 4)
         return NUFDS_EINVAL;
-    if (prm->precision != NUFDS_FP32) return NUFDS_EUNSUPPORTED;
+    if (prm->precision != NUFDS_FP32 && prm->precision != NUFDS_FP16_STORE &&
+        prm->precision != NUFDS_BF16_STORE)
+        return NUFDS_EINVAL;
     if (!fft_size_ok(prm->nx) || !fft_size_ok(prm->ny)) return NUFDS_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     nufds_plan *P = new (std::nothrow) nufds_plan();
@@ -506,6 +556,7 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     P->nx = prm->nx;
     P->ny = prm->ny;
     P->budget = prm->hbm_budget_bytes;
+    P->prec = prm->precision;
     int rc;
     if ((rc = fft_plan_get(P->nx, &P->fx)) || (rc = fft_plan_get(P->ny, &P->fy))) {
         free_plan(P);
@@ -526,7 +577,7 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     P->pb_nkx = (int)(V.khi_x - V.klo_x + 1);
     P->pb_nky = (int)(V.khi_y - V.klo_y + 1);
     const size_t npb = (size_t)P->pb_nkx * P->pb_nky, npix = (size_t)P->nx * P->ny;
-    P->fixed_bytes = npb * 12 + npix * 12 + npix * 32;
+    P->fixed_bytes = npb * 12 + npix * 12 + npix * 4 * prec_bytes(P->prec) + 64;
     if (P->budget && P->fixed_bytes > P->budget) {
         free_plan(P);
         return NUFDS_ENOMEM;
@@ -535,11 +586,13 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
         cudaMalloc(&P->pb_frac, npb * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&P->rm_base, npix * sizeof(short2)) != cudaSuccess ||
         cudaMalloc(&P->rm_frac, npix * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&P->G, 4 * npix * sizeof(float2)) != cudaSuccess) {
+        cudaMalloc(&P->G, 4 * npix * prec_bytes(P->prec)) != cudaSuccess ||
+        cudaMalloc(&P->sc, 256) != cudaSuccess) {
         cudaGetLastError();
         free_plan(P);
         return NUFDS_ENOMEM;
     }
+    P->acc = (double *)(P->sc + 16);
     // FP64 tables: inverse stretch on the full-view band; output map on the
     // full-view pixel lattice (computed at z = 1, valid at every z)
     const double B1 = full_width(P->lam, P->pitch, 1.0);
@@ -805,9 +858,11 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     }
     // oversampled spectrum of the hologram
     const float2 *H = (const float2 *)d_holo;
-    if ((rc = launch_rows_pad2(fx, H, nx, A, 2 * nx, ny, st)) ||
-        (rc = launch_transpose(A, 2 * nx, Bf, ny, ny, 2 * nx, st)) ||
-        (rc = launch_rows_pad2(fy, Bf, ny, G, 2 * ny, 2 * nx, st)))
+    if ((rc = launch_rows_pad2(fx, H, PREC_F32, nx, A, PREC_F32, 2 * nx, ny, nullptr, nullptr,
+                               st)) ||
+        (rc = launch_transpose(A, 2 * nx, Bf, ny, ny, 2 * nx, PREC_F32, st)) ||
+        (rc = launch_rows_pad2(fy, Bf, PREC_F32, ny, G, PREC_F32, 2 * ny, 2 * nx, nullptr,
+                               nullptr, st)))
         return rc;
     // the view
     if ((rc = launch_chirp_table(fpx, nx * g.pitch, g.lam, V.z, chx, st)) ||
@@ -838,10 +893,16 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     sa.npx = V.npx;
     sa.npy = V.npy;
     sa.S = Bf;
+    sa.prec = PREC_F32;
+    sa.sc_g = nullptr;
+    sa.sc_s = nullptr;
+    sa.energy = nullptr;
     if ((rc = launch_stretch(sa, st)) ||
-        (rc = launch_rows_view(fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, grid_y, st)) ||
-        (rc = launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, st)) ||
-        (rc = launch_rows_view(fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr, grid_x, st)))
+        (rc = launch_rows_view(fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, grid_y, PREC_F32,
+                               nullptr, nullptr, st)) ||
+        (rc = launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, PREC_F32, st)) ||
+        (rc = launch_rows_view(fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr, grid_x,
+                               PREC_F32, nullptr, nullptr, st)))
         return rc;
     RemapArgs ra;
     ra.Q = A;
@@ -864,5 +925,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     ra.kappa_x = (float)kx;
     ra.kappa_y = (float)ky;
     ra.out = d_out;
+    ra.prec = PREC_F32;
+    ra.sc_q = nullptr;
     return launch_remap(ra, st);
 }

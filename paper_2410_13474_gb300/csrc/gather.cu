@@ -30,13 +30,16 @@ __device__ __forceinline__ int wrap(int m, int M) {
     return m < 0 ? m + M : m;
 }
 
+template <class T>
 __global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
+    const T *G = (const T *)a.G;
+    const float ginv = a.sc_g ? 1.0f / *a.sc_g : 1.0f, ssc = a.sc_s ? *a.sc_s : 1.0f;
     const int jy = blockIdx.x * 32 + threadIdx.x;
     const int jx = blockIdx.y * 8 + threadIdx.y;
-    if (jx >= a.npx || jy >= a.npy) return;
+    const bool valid = jx < a.npx && jy < a.npy;
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
     float2 acc = make_float2(0.f, 0.f);
-    if (kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
+    if (valid && kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
         const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
         const short2 b = a.pb_base[t];
         if (b.x != kMasked) {
@@ -54,11 +57,11 @@ __global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
             for (int j = 0; j < kW; ++j) cols[j] = wrap(my0 + j, My);
 #pragma unroll
             for (int i = 0; i < kW; ++i) {
-                const float2 *row = a.G + (long)wrap(mx0 + i, Mx) * My;
+                const long row = (long)wrap(mx0 + i, Mx) * My;
                 float2 r = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < kW; ++j) {
-                    float2 g = __ldg(row + cols[j]);
+                    float2 g = ld_c(G, row + cols[j], 1.0f);
                     r.x = fmaf(wy[j], g.x, r.x);
                     r.y = fmaf(wy[j], g.y, r.y);
                 }
@@ -67,12 +70,21 @@ __global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
             }
             // (-1)^(jx + jy): centring of the inverse transforms that follow
             if ((jx + jy) & 1) acc = make_float2(-acc.x, -acc.y);
+            acc = make_float2(acc.x * ginv, acc.y * ginv);
         }
     }
-    a.S[(long)jx * a.npy + jy] = acc;
+    if (valid) st_c((T *)a.S, (long)jx * a.npy + jy, acc, ssc);
+    if (a.energy) {  // uniform over the launch; every lane reaches the shuffles
+        double e = (double)acc.x * acc.x + (double)acc.y * acc.y;
+        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(a.energy, e);
+    }
 }
 
+template <class T>
 __global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
+    const T *Q = (const T *)a.Q;
+    const float qinv = a.sc_q ? 1.0f / *a.sc_q : 1.0f;
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
     if (i >= a.ox || j >= a.oy) return;
@@ -94,17 +106,18 @@ __global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < kW; ++p) {
-        const float2 *row = a.Q + (long)wrap(my0 + p, My) * Mx;
+        const long row = (long)wrap(my0 + p, My) * Mx;
         float2 r = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < kW; ++q) {
-            float2 g = __ldg(row + cols[q]);
+            float2 g = ld_c(Q, row + cols[q], 1.0f);
             r.x = fmaf(wx[q], g.x, r.x);
             r.y = fmaf(wx[q], g.y, r.y);
         }
         acc.x = fmaf(wy[p], r.x, acc.x);
         acc.y = fmaf(wy[p], r.y, acc.y);
     }
+    acc = make_float2(acc.x * qinv, acc.y * qinv);
     const long o = (long)j * a.ox + i;
     if (a.kind == 0) {
         ((float *)a.out)[o] = fmaf(acc.x, acc.x, acc.y * acc.y);
@@ -124,14 +137,18 @@ __global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
 
 int launch_stretch(const StretchArgs &a, cudaStream_t st) {
     dim3 grid((a.npy + 31) / 32, (a.npx + 7) / 8);
-    k_stretch<<<grid, dim3(32, 8), 0, st>>>(a);
+    if (a.prec == PREC_F32) k_stretch<float2><<<grid, dim3(32, 8), 0, st>>>(a);
+    else if (a.prec == PREC_F16) k_stretch<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
+    else k_stretch<__nv_bfloat162><<<grid, dim3(32, 8), 0, st>>>(a);
     count_launch();
     return check_launch();
 }
 
 int launch_remap(const RemapArgs &a, cudaStream_t st) {
     dim3 grid((a.ox + 31) / 32, (a.oy + 7) / 8);
-    k_remap<<<grid, dim3(32, 8), 0, st>>>(a);
+    if (a.prec == PREC_F32) k_remap<float2><<<grid, dim3(32, 8), 0, st>>>(a);
+    else if (a.prec == PREC_F16) k_remap<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
+    else k_remap<__nv_bfloat162><<<grid, dim3(32, 8), 0, st>>>(a);
     count_launch();
     return check_launch();
 }

@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA sources of libnufds (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,9 +18,27 @@ constexpr int kW = 8;
 constexpr double kBeta = 2.30 * kW;
 constexpr int kSigma = 2;
 
-struct c64 {
-    float x, y;
-};
+// Storage of the cached spectrum and the inter-pass arrays (arithmetic is FP32).
+enum Prec { PREC_F32 = 0, PREC_F16 = 1, PREC_BF16 = 2 };
+inline size_t prec_bytes(int prec) { return prec == PREC_F32 ? 8 : 4; }
+
+// load/store of one complex sample in a storage type; FP16 samples are held
+// multiplied by a power-of-two scale (sc on store, inv = 1/sc on load)
+__device__ __forceinline__ float2 ld_c(const float2 *p, long i, float) { return __ldg(p + i); }
+__device__ __forceinline__ float2 ld_c(const __half2 *p, long i, float inv) {
+    float2 v = __half22float2(__ldg(p + i));
+    return make_float2(v.x * inv, v.y * inv);
+}
+__device__ __forceinline__ float2 ld_c(const __nv_bfloat162 *p, long i, float) {
+    return __bfloat1622float2(__ldg(p + i));
+}
+__device__ __forceinline__ void st_c(float2 *p, long i, float2 v, float) { p[i] = v; }
+__device__ __forceinline__ void st_c(__half2 *p, long i, float2 v, float sc) {
+    p[i] = __float22half2_rn(make_float2(v.x * sc, v.y * sc));
+}
+__device__ __forceinline__ void st_c(__nv_bfloat162 *p, long i, float2 v, float) {
+    p[i] = __float22bfloat162_rn(v);
+}
 
 // Entry of a coordinate table: a point on a fine (2x oversampled) grid as
 // centred integer base (floor of 2t) and fraction in [0, 1).
@@ -38,6 +58,7 @@ struct FftPlan {
     int prefix[kMaxPasses] = {};   // r_1 ... r_{j-1}
     int threads = 0;
     int ncoarse = 0;                   // ceil(L / 64)
+    double dmax = 0;                   // max_n 1 / psi_hat(n - L/2)
     size_t smem_bytes = 0;
     // device tables (owned by the length cache, or caller memory)
     const float2 *tw = nullptr;        // W_L^j (j < 64) | W_L^{64 i} (i < ncoarse)
@@ -67,21 +88,24 @@ int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pa
 //   out[r][2k + a] = (-1)^k sum_n in[r][n] pre[n] e^{-i pi a (n - L/2)/L} e^{-2 pi i n k/L}
 // with pre = pad_pre.  This is the centred DFT on the 2x oversampled grid of
 // the deapodised row.
-int launch_rows_pad2(const FftPlan &p, const float2 *in, long in_ld, float2 *out, long out_ld,
-                     int rows, cudaStream_t st);
+// in_prec: storage of in (PREC_F32 for the hologram); out: storage prec.
+// sc_in / sc_out: device pointers to the FP16 scales of in and out (ignored otherwise).
+int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
+                     int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
+                     cudaStream_t st);
 
 // View pass: rows of length L: inverse centred DFT (input already carries
 // (-1)^k), multiply by chirp[n] (complex, includes deapodisation and 1/L),
 // then the padded forward pass as above (output 2L per row).  scratch holds
 // grid-size * L float2.
-int launch_rows_view(const FftPlan &p, const float2 *in, long in_ld, const float2 *chirp,
-                     float2 *out, long out_ld, int rows, float2 *scratch, int grid,
-                     cudaStream_t st);
+int launch_rows_view(const FftPlan &p, const void *in, long in_ld, const float2 *chirp, void *out,
+                     long out_ld, int rows, float2 *scratch, int grid, int prec,
+                     const float *sc_in, const float *sc_out, cudaStream_t st);
 int rows_view_grid(const FftPlan &p, int rows);
 
 // out[c][r] = in[r][c]
-int launch_transpose(const float2 *in, long in_ld, float2 *out, long out_ld, int rows, int cols,
-                     cudaStream_t st);
+int launch_transpose(const void *in, long in_ld, void *out, long out_ld, int rows, int cols,
+                     int prec, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // FP64 maps and tables (maps.cu)
@@ -109,7 +133,7 @@ int launch_outchirp_table(double kappa, long b0, int nb, float2 *E, cudaStream_t
 // Gathers (gather.cu)
 // ---------------------------------------------------------------------------
 struct StretchArgs {
-    const float2 *G;        // oversampled spectrum, layout [mx][my], 2Nx x 2Ny
+    const void *G;          // oversampled spectrum, layout [mx][my], 2Nx x 2Ny
     int Nx, Ny;
     const short2 *pb_base;  // pull-back table, layout [kx][ky]
     const float2 *pb_frac;
@@ -117,12 +141,15 @@ struct StretchArgs {
     int pb_nkx, pb_nky;
     long klo_x, khi_x, klo_y, khi_y, kc_x, kc_y;
     int npx, npy;
-    float2 *S;              // output, layout [jx][jy], npx x npy
+    void *S;                // output, layout [jx][jy], npx x npy
+    int prec;               // storage of G and S
+    const float *sc_g, *sc_s;
+    double *energy;         // if not null: += sum |S|^2 (before storage rounding)
 };
 int launch_stretch(const StretchArgs &a, cudaStream_t st);
 
 struct RemapArgs {
-    const float2 *Q;        // oversampled FrT output, layout [my][mx], 2npy x 2npx
+    const void *Q;          // oversampled FrT output, layout [my][mx], 2npy x 2npx
     int npx, npy;
     long kc_x, kc_y;
     const short2 *rm_base;  // output-map table, layout [j][i], row length rm_ld
@@ -134,8 +161,20 @@ struct RemapArgs {
     long ex_b0, ey_b0;
     float kappa_x, kappa_y;
     void *out;
+    int prec;               // storage of Q
+    const float *sc_q;
 };
 int launch_remap(const RemapArgs &a, cudaStream_t st);
+
+// FP16 scales (device floats sc[]) from exact energy bounds (max |.| <= the
+// Frobenius norm, which Parseval gives for every DFT stage):
+//   sc[0] T1, sc[1] G, sc[2] S, sc[3] T_T, sc[4] T, sc[5] Q; each the largest
+//   power of two with scale * bound <= 2^15.  acc[] (device doubles): [0], [1]
+//   weighted hologram energies (launch_norms), [2] ||S||^2 (the stretch).
+int launch_norms(const float2 *H, int nx, int ny, const double *dx, const double *dy, double *acc,
+                 cudaStream_t st);
+int launch_scales_load(float *sc, const double *acc, int nx, int ny, double k2, cudaStream_t st);
+int launch_scales_view(float *sc, const double *acc, double dxp, double dyp, cudaStream_t st);
 
 // launch bookkeeping
 void count_launch();
