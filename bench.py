@@ -344,15 +344,95 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched workload: 8 holograms of uneven size, 64 partial views of uneven
+    size, position and depth.  One batched call (per-stage persistent kernels
+    inside one CUDA graph per wave) against the same 64 views as sequential
+    single-view calls; views/s and output Mpix/s of each."""
+    import torch
+
+    import paper_2410_13474_gb300 as nf
+    import synth
+    from synth.configs import batch_workload
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2410_13474_gb300 import build as b
+    b.build()
+    holos, reqs = batch_workload()
+    t0 = time.time()
+    plans = []
+    for w in holos:
+        h = synth.gpu_hologram(w.point_cloud(), w.wavelength, w.pitch, w.n, w.n)
+        plans.append(nf.Plan(w.wavelength, w.pitch, w.n, w.n, h))
+        del h
+    torch.cuda.synchronize()
+    init_s = time.time() - t0
+    views, vplans, outs = [], [], []
+    for r in reqs:
+        w, pl = holos[r.holo], plans[r.holo]
+        p = pl.view_plan(nf.View(z=r.z))["pitch_out_x_m"]
+        v = nf.View(z=r.z, center_x=r.dx * p, center_y=r.dy * p, width=r.size * p,
+                    height=r.size * p, out_nx=r.size, out_ny=r.size)
+        views.append(v)
+        vplans.append(pl)
+        outs.append(pl.output_like(v))
+    seq_outs = [torch.empty_like(o) for o in outs]
+    pix = sum(r.size * r.size for r in reqs)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def batched():
+        st = nf.reconstruct_batch(vplans, views, outs)
+        assert all(s == 0 for s in st), st
+
+    def sequential():
+        for pl, v, o in zip(vplans, views, seq_outs):
+            pl.reconstruct(v, o)
+
+    res = {}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        nf.launch_count(reset=True)
+        ev0.record(stream)
+        k = max(2, args.steps // 4)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / k
+        res[name] = {"ms_per_batch": round(ms, 3), "views_per_s": round(len(reqs) / (ms * 1e-3), 2),
+                     "Mpix_per_s": round(pix / (ms * 1e-3) / 1e6, 2), "launches_per_batch":
+                     nf.launch_count() // k, "batches": k}
+    same = all(torch.equal(a, b2) for a, b2 in zip(outs, seq_outs))
+    line = {"metric": "batched partial views/s (64 views, 8 holograms)",
+            "value": res["batched"]["views_per_s"], "unit": "views/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch-64-views-8-holograms",
+                       "holograms": [[w.n, round(w.pitch * 1e6, 4), w.n_points] for w in holos],
+                       "view_sizes": sorted({r.size for r in reqs}), "views": len(reqs),
+                       "output_Mpix_per_batch": round(pix / 1e6, 2)},
+            "batched": res["batched"], "sequential": res["sequential"],
+            "speedup": round(res["sequential"]["ms_per_batch"] / res["batched"]["ms_per_batch"], 3),
+            "batched_equals_sequential_bitwise": bool(same), "init_s": round(init_s, 1)}
+    print(json.dumps(line), flush=True)
+    for pl in plans:
+        pl.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uwa16k", choices=["uwa16k", "wa4096", "small512"])
+    ap.add_argument("--workload", default="uwa16k",
+                    choices=["uwa16k", "wa4096", "small512", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == "batch64":
+        return run_batch(args)
     w = _workload(args.workload)
     if args.impl == "reference":
         run_reference(args, w)

@@ -10,6 +10,8 @@
 //   rows_pad2 along x, transpose, rows_pad2 along y -> G[mx][my]
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <list>
@@ -25,8 +27,22 @@
 namespace nufds {
 
 static thread_local int64_t t_launches = 0;
+
+// With NUFDS_DEBUG set, report the CUDA error behind an NUFDS_ECUDA return.
+static int cuda_fail(const char *what, int line) {
+    cudaError_t e = cudaGetLastError();
+    if (getenv("NUFDS_DEBUG"))
+        fprintf(stderr, "nufds: %s failed at api.cu:%d: %s\n", what, line, cudaGetErrorString(e));
+    return NUFDS_ECUDA;
+}
+#define CUDA_FAIL(what) cuda_fail(what, __LINE__)
 void count_launch() { ++t_launches; }
-int check_launch() { return cudaPeekAtLastError() == cudaSuccess ? 0 : NUFDS_ECUDA; }
+int check_launch() {
+    cudaError_t e = cudaPeekAtLastError();
+    if (e == cudaSuccess) return 0;
+    if (getenv("NUFDS_DEBUG")) fprintf(stderr, "nufds: launch error: %s\n", cudaGetErrorString(e));
+    return NUFDS_ECUDA;
+}
 
 struct ViewPlan {
     int ox, oy;
@@ -511,6 +527,447 @@ static bool fft_size_ok(int n) {
     return m == 1;
 }
 
+// ---------------------------------------------------------------------------
+// Batched reconstruction: many views (of one or several plans, of uneven
+// sizes) per launch.  Views are grouped into waves that fit the batch
+// workspace; each wave is one CUDA graph: the per-view FP64 tables, then one
+// persistent launch per stage over all views' work items (stretch tiles, row
+// passes, transpose tiles, remap tiles).
+// ---------------------------------------------------------------------------
+struct BatchView {
+    int idx;
+    nufds_plan *P;
+    ViewPlan V;
+    const FftPlan *fpx, *fpy;
+    int kind;
+    void *out;
+    size_t off, bytes;  // region in the batch workspace
+};
+
+struct BatchWs {
+    char *dev = nullptr;
+    size_t bytes = 0;
+    // pinned descriptor staging: a ring of buffers, each reused only after
+    // the upload that last read it has executed
+    static constexpr int kRing = 4;
+    char *host[kRing] = {};
+    size_t host_bytes[kRing] = {};
+    cudaEvent_t host_ev[kRing] = {};
+    int ring = 0;
+    struct Graph {
+        std::string key;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::list<Graph> graphs;
+    cudaStream_t cap = nullptr;  // private stream the graphs are captured on
+};
+static std::mutex g_batch_mu;
+static std::map<int, BatchWs *> g_batch;
+
+static size_t batch_cap_bytes() {
+    const char *e = getenv("NUFDS_BATCH_WS_GB");
+    double gb = e ? atof(e) : 48.0;
+    return (size_t)(gb * (1ull << 30));
+}
+
+static size_t view_batch_bytes(const BatchView &b, int prec) {
+    const size_t np = (size_t)b.V.npx * b.V.npy, eb = prec_bytes(prec);
+    size_t t = align256(eb * 4 * np) + align256(eb * 2 * np) +
+               align256(sizeof(float2) * (b.V.npx + b.V.npy)) + 256;
+    if (b.kind == NUFDS_OUT_FIELD_C64)
+        t += align256(sizeof(float2) * (4 * (b.V.khi_x - b.V.klo_x) + 4 * (b.V.khi_y - b.V.klo_y) + 68));
+    if (!b.V.lattice) t += 2 * align256((sizeof(short2) + sizeof(float2)) * (size_t)b.V.ox * b.V.oy);
+    return t;
+}
+
+static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_t *statuses) {
+    // ---- sizes and the workspace
+    int maxL = 0, threads = 64;
+    size_t smem = 0, views_bytes = 0;
+    std::vector<const FftPlan *> fps;
+    auto fidx = [&](const FftPlan *f) {
+        for (size_t i = 0; i < fps.size(); ++i)
+            if (fps[i] == f) return (int)i;
+        fps.push_back(f);
+        return (int)fps.size() - 1;
+    };
+    int rows_y = 0, rows_x = 0;
+    for (auto &b : w) {
+        for (const FftPlan *f : {b.fpx, b.fpy}) {
+            maxL = std::max(maxL, f->L);
+            threads = std::max(threads, f->threads);
+            smem = std::max(smem, f->smem_bytes);
+            fidx(f);
+        }
+        b.off = views_bytes;
+        b.bytes = view_batch_bytes(b, prec);
+        views_bytes += b.bytes;
+        rows_y += b.V.npx;
+        rows_x += 2 * b.V.npy;
+    }
+    const int n = (int)w.size();
+    const int grid = rows_view_batch_grid(threads, smem, std::max(rows_y, rows_x));
+    const size_t scr_bytes = align256(sizeof(float2) * (size_t)grid * maxL);
+    // descriptors: PassArgs[], RowItem[2n], row offsets, TrItem[n], tile offsets,
+    // StretchArgs[n], RemapArgs[n], offsets
+    const size_t desc_bytes = align256(sizeof(PassArgs) * fps.size()) +
+                              align256(sizeof(RowItem) * 2 * n) + align256(sizeof(int) * 2 * (n + 1)) +
+                              align256(sizeof(TrItem) * n) + align256(sizeof(int) * (n + 1)) +
+                              align256(sizeof(StretchArgs) * n) + align256(sizeof(int) * (n + 1)) +
+                              align256(sizeof(RemapArgs) * n) + align256(sizeof(int) * (n + 1));
+    const size_t need = views_bytes + scr_bytes + desc_bytes;
+    int dev;
+    cudaGetDevice(&dev);
+    BatchWs *B;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        B = g_batch[dev];
+        if (!B) B = g_batch[dev] = new BatchWs();
+    }
+    if (need > B->bytes) {
+        cudaStreamSynchronize(st);
+        for (auto &g : B->graphs) cudaGraphExecDestroy(g.exec);
+        B->graphs.clear();
+        cudaFree(B->dev);
+        B->dev = nullptr;
+        B->bytes = 0;
+        if (cudaMalloc(&B->dev, need) != cudaSuccess) {
+            cudaGetLastError();
+            return NUFDS_ENOMEM;
+        }
+        B->bytes = need;
+    }
+    const int slot = B->ring;
+    B->ring = (B->ring + 1) % BatchWs::kRing;
+    if (B->host_ev[slot]) cudaEventSynchronize(B->host_ev[slot]);
+    else if (cudaEventCreateWithFlags(&B->host_ev[slot], cudaEventDisableTiming) != cudaSuccess)
+        return CUDA_FAIL("cudaEventCreate");
+    if (desc_bytes > B->host_bytes[slot]) {
+        cudaFreeHost(B->host[slot]);
+        B->host[slot] = nullptr;
+        if (cudaMallocHost(&B->host[slot], desc_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            B->host_bytes[slot] = 0;
+            return NUFDS_ENOMEM;
+        }
+        B->host_bytes[slot] = desc_bytes;
+    }
+    char *dbase = B->dev, *scr_base = dbase + views_bytes, *ddesc = scr_base + scr_bytes;
+    char *hdesc = B->host[slot];
+    // ---- descriptors (host), mirrored at ddesc
+    size_t o = 0;
+    auto carve = [&](size_t bytes) { size_t r = o; o += align256(bytes); return r; };
+    const size_t o_pa = carve(sizeof(PassArgs) * fps.size()), o_ri = carve(sizeof(RowItem) * 2 * n),
+                 o_roff = carve(sizeof(int) * 2 * (n + 1)), o_tr = carve(sizeof(TrItem) * n),
+                 o_toff = carve(sizeof(int) * (n + 1)), o_sa = carve(sizeof(StretchArgs) * n),
+                 o_soff = carve(sizeof(int) * (n + 1)), o_ra = carve(sizeof(RemapArgs) * n),
+                 o_roff2 = carve(sizeof(int) * (n + 1));
+    PassArgs *hpa = (PassArgs *)(hdesc + o_pa);
+    RowItem *hri = (RowItem *)(hdesc + o_ri);
+    int *hroff = (int *)(hdesc + o_roff);
+    TrItem *htr = (TrItem *)(hdesc + o_tr);
+    int *htoff = (int *)(hdesc + o_toff);
+    StretchArgs *hsa = (StretchArgs *)(hdesc + o_sa);
+    int *hsoff = (int *)(hdesc + o_soff);
+    RemapArgs *hra = (RemapArgs *)(hdesc + o_ra);
+    int *hrmoff = (int *)(hdesc + o_roff2);
+    for (size_t i = 0; i < fps.size(); ++i) hpa[i] = fft_pass_args(*fps[i]);
+    const size_t eb = prec_bytes(prec);
+    struct Regions {
+        void *A, *Bf;
+        float2 *chx, *chy, *Ex, *Ey;
+        short2 *rmb;
+        float2 *rmf;
+        float *sc;
+        double *acc;
+        long ex_b0, ey_b0;
+        int nbx, nby;
+    };
+    std::vector<Regions> R(n);
+    int ty = 0, tx = 0, ttr = 0, tst = 0, trm = 0;
+    for (int i = 0; i < n; ++i) {
+        BatchView &b = w[i];
+        const ViewPlan &V = b.V;
+        nufds_plan *P = b.P;
+        char *p = dbase + b.off;
+        const size_t np = (size_t)V.npx * V.npy;
+        Regions &g = R[i];
+        g.A = p;
+        p += align256(eb * 4 * np);
+        g.Bf = p;
+        p += align256(eb * 2 * np);
+        g.chx = (float2 *)p;
+        g.chy = g.chx + V.npx;
+        p += align256(sizeof(float2) * (V.npx + V.npy));
+        g.sc = (float *)p;
+        g.acc = (double *)(p + 64);
+        p += 256;
+        g.ex_b0 = 2 * V.klo_x - 8;
+        g.ey_b0 = 2 * V.klo_y - 8;
+        g.nbx = (int)(2 * (V.khi_x - V.klo_x) + 17);
+        g.nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
+        g.Ex = g.Ey = nullptr;
+        if (b.kind == NUFDS_OUT_FIELD_C64) {
+            g.Ex = (float2 *)p;
+            g.Ey = g.Ex + g.nbx;
+            p += align256(sizeof(float2) * (4 * (V.khi_x - V.klo_x) + 4 * (V.khi_y - V.klo_y) + 68));
+        }
+        g.rmb = P->rm_base;
+        g.rmf = P->rm_frac;
+        long rm_ld = P->nx, rm_i0 = 0, rm_j0 = 0;
+        if (V.lattice) {
+            rm_i0 = V.i0;
+            rm_j0 = V.j0;
+        } else {
+            g.rmf = (float2 *)p;
+            g.rmb = (short2 *)(p + align256(sizeof(float2) * (size_t)V.ox * V.oy));
+            rm_ld = V.ox;
+        }
+        const float *scG = prec == NUFDS_FP16_STORE ? P->sc + 1 : nullptr;
+        const float *scS = prec == NUFDS_FP16_STORE ? P->sc + 2 : nullptr;
+        const float *scT = prec == NUFDS_FP16_STORE ? g.sc + 3 : nullptr;
+        const float *scQ = prec == NUFDS_FP16_STORE ? g.sc + 5 : nullptr;
+        StretchArgs &sa = hsa[i];
+        sa.G = P->G;
+        sa.Nx = P->nx;
+        sa.Ny = P->ny;
+        sa.pb_base = P->pb_base;
+        sa.pb_frac = P->pb_frac;
+        sa.pb_kx0 = P->pb_kx0;
+        sa.pb_ky0 = P->pb_ky0;
+        sa.pb_nkx = P->pb_nkx;
+        sa.pb_nky = P->pb_nky;
+        sa.klo_x = V.klo_x;
+        sa.khi_x = V.khi_x;
+        sa.klo_y = V.klo_y;
+        sa.khi_y = V.khi_y;
+        sa.kc_x = V.kc_x;
+        sa.kc_y = V.kc_y;
+        sa.npx = V.npx;
+        sa.npy = V.npy;
+        sa.S = g.Bf;
+        sa.prec = prec;
+        sa.sc_g = scG;
+        sa.sc_s = scS;
+        sa.energy = prec == NUFDS_FP16_STORE ? g.acc + 2 : nullptr;
+        hsoff[i] = tst;
+        tst += stretch_tiles(V.npx, V.npy);
+        RowItem &ry = hri[i];
+        ry.in = g.Bf;
+        ry.out = g.A;
+        ry.chirp = g.chy;
+        ry.in_ld = V.npy;
+        ry.out_ld = 2 * V.npy;
+        ry.args = fidx(b.fpy);
+        ry.sc_in = scS;
+        ry.sc_out = scT;
+        hroff[i] = ty;
+        ty += V.npx;
+        RowItem &rx = hri[n + i];
+        rx.in = g.Bf;
+        rx.out = g.A;
+        rx.chirp = g.chx;
+        rx.in_ld = V.npx;
+        rx.out_ld = 2 * V.npx;
+        rx.args = fidx(b.fpx);
+        rx.sc_in = scT;
+        rx.sc_out = scQ;
+        hroff[n + 1 + i] = tx;
+        tx += 2 * V.npy;
+        TrItem &tr = htr[i];
+        tr.in = g.A;
+        tr.out = g.Bf;
+        tr.in_ld = 2 * V.npy;
+        tr.out_ld = V.npx;
+        tr.rows = V.npx;
+        tr.cols = 2 * V.npy;
+        tr.tiles_x = (tr.cols + 31) / 32;
+        htoff[i] = ttr;
+        ttr += tr.tiles_x * ((tr.rows + 31) / 32);
+        RemapArgs &ra = hra[i];
+        ra.Q = g.A;
+        ra.npx = V.npx;
+        ra.npy = V.npy;
+        ra.kc_x = V.kc_x;
+        ra.kc_y = V.kc_y;
+        ra.rm_base = g.rmb;
+        ra.rm_frac = g.rmf;
+        ra.rm_ld = rm_ld;
+        ra.rm_i0 = rm_i0;
+        ra.rm_j0 = rm_j0;
+        ra.ox = V.ox;
+        ra.oy = V.oy;
+        ra.kind = b.kind;
+        ra.Ex = g.Ex;
+        ra.Ey = g.Ey;
+        ra.ex_b0 = g.ex_b0;
+        ra.ey_b0 = g.ey_b0;
+        ra.kappa_x = (float)(M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch)));
+        ra.kappa_y = (float)(M_PI * P->lam * V.z / ((P->ny * P->pitch) * (P->ny * P->pitch)));
+        ra.out = b.out;
+        ra.prec = prec;
+        ra.sc_q = scQ;
+        hrmoff[i] = trm;
+        trm += remap_tiles(V.ox, V.oy);
+    }
+    hroff[n] = ty;
+    hroff[2 * n + 1] = tx;
+    htoff[n] = ttr;
+    hsoff[n] = tst;
+    hrmoff[n] = trm;
+    // the upload is outside the graph; the graph reads ddesc
+    if (cudaMemcpyAsync(ddesc, hdesc, o, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaEventRecord(B->host_ev[slot], st) != cudaSuccess)
+        return CUDA_FAIL("descriptor upload");
+    const PassArgs *dpa = (const PassArgs *)(ddesc + o_pa);
+    const RowItem *dri = (const RowItem *)(ddesc + o_ri);
+    const int *droff = (const int *)(ddesc + o_roff);
+    // ---- the graph: key = the descriptor bytes and the table-launch parameters
+    std::string key(hdesc, o);
+    key.append((const char *)&dbase, sizeof(dbase));
+    for (int i = 0; i < n; ++i) {
+        key.append((const char *)&w[i].V, sizeof(ViewPlan));
+        key.append((const char *)&w[i].kind, sizeof(int));
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto it = B->graphs.begin(); it != B->graphs.end(); ++it)
+        if (it->key == key) {
+            exec = it->exec;
+            B->graphs.splice(B->graphs.begin(), B->graphs, it);
+            break;
+        }
+    if (!exec) {
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph is launched on st
+        if (!B->cap && cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess)
+            return CUDA_FAIL("cudaStreamCreate");
+        const cudaStream_t caller = st;
+        st = B->cap;
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return CUDA_FAIL("cudaStreamBeginCapture");
+        int rc = 0;
+        for (int i = 0; i < n && !rc; ++i) {
+            BatchView &b = w[i];
+            nufds_plan *P = b.P;
+            const ViewPlan &V = b.V;
+            Regions &g = R[i];
+            rc = launch_chirp_table(*b.fpx, P->nx * P->pitch, P->lam, V.z, g.chx, st);
+            if (!rc) rc = launch_chirp_table(*b.fpy, P->ny * P->pitch, P->lam, V.z, g.chy, st);
+            if (!rc && b.kind == NUFDS_OUT_FIELD_C64) {
+                const double kx = M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch));
+                const double ky = M_PI * P->lam * V.z / ((P->ny * P->pitch) * (P->ny * P->pitch));
+                rc = launch_outchirp_table(kx, g.ex_b0, g.nbx, g.Ex, st);
+                if (!rc) rc = launch_outchirp_table(ky, g.ey_b0, g.nby, g.Ey, st);
+            }
+            if (!rc && !V.lattice)
+                rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px, V.py,
+                                        V.ox, V.oy, g.rmb, g.rmf, st);
+            if (!rc && prec == NUFDS_FP16_STORE &&
+                cudaMemsetAsync(g.acc, 0, 4 * sizeof(double), st) != cudaSuccess)
+                rc = NUFDS_ECUDA;
+        }
+        const char *where = "tables";
+        if (!rc && (where = "stretch"))
+            rc = launch_stretch_batch((const StretchArgs *)(ddesc + o_sa),
+                                      (const int *)(ddesc + o_soff), n, tst, prec, st);
+        for (int i = 0; i < n && !rc && prec == NUFDS_FP16_STORE; ++i)
+            rc = launch_scales_view(R[i].sc, R[i].acc, w[i].fpx->dmax, w[i].fpy->dmax, st);
+        if (!rc && (where = "rows_y"))
+            rc = launch_rows_view_batch(dpa, dri, droff, n, ty, threads, smem,
+                                        (float2 *)scr_base, maxL, grid, prec, st);
+        if (!rc && (where = "transpose"))
+            rc = launch_transpose_batch((const TrItem *)(ddesc + o_tr),
+                                        (const int *)(ddesc + o_toff), n, ttr, prec, st);
+        if (!rc && (where = "rows_x"))
+            rc = launch_rows_view_batch(dpa, dri + n, droff + n + 1, n, tx, threads, smem,
+                                        (float2 *)scr_base, maxL, grid, prec, st);
+        if (!rc && (where = "remap"))
+            rc = launch_remap_batch((const RemapArgs *)(ddesc + o_ra),
+                                    (const int *)(ddesc + o_roff2), n, trm, prec, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (rc || ce != cudaSuccess) {
+            if (ce == cudaSuccess) cudaGraphDestroy(graph);
+            if (getenv("NUFDS_DEBUG"))
+                fprintf(stderr, "nufds: batch capture stage %s (threads %d smem %zu grid %d)\n",
+                        where, threads, smem, grid);
+            int r2 = CUDA_FAIL(rc ? "a launch during capture" : "cudaStreamEndCapture");
+            return rc ? rc : r2;
+        }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return CUDA_FAIL("cudaGraphInstantiate");
+        B->graphs.push_front({key, exec});
+        if (B->graphs.size() > 16) {
+            cudaGraphExecDestroy(B->graphs.back().exec);
+            B->graphs.pop_back();
+        }
+        st = caller;
+    }
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) return CUDA_FAIL("cudaGraphLaunch");
+    count_launch();
+    for (auto &b : w)
+        if (statuses) statuses[b.idx] = NUFDS_OK;
+    return NUFDS_OK;
+}
+
+static int batch_impl(nufds_plan *const *plans, const nufds_view *views, void *const *outs,
+                      int32_t count, cudaStream_t st, int32_t *statuses) {
+    int first = NUFDS_OK;
+    auto fail = [&](int i, int rc) {
+        if (statuses) statuses[i] = rc;
+        if (first == NUFDS_OK) first = rc;
+    };
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NUFDS_ECUDA;
+    std::vector<BatchView> all;
+    for (int32_t i = 0; i < count; ++i) {
+        nufds_plan *P = plans[i];
+        if (!P || !outs[i] || !P->loaded || P->device != dev) {
+            fail(i, NUFDS_EINVAL);
+            continue;
+        }
+        BatchView b;
+        b.idx = i;
+        b.P = P;
+        b.kind = views[i].out_kind;
+        b.out = outs[i];
+        int rc = plan_view_cached(P, &views[i], &b.V);
+        if (!rc && (b.V.klo_x < P->pb_kx0 || b.V.khi_x >= P->pb_kx0 + P->pb_nkx ||
+                    b.V.klo_y < P->pb_ky0 || b.V.khi_y >= P->pb_ky0 + P->pb_nky))
+            rc = NUFDS_EUNSUPPORTED;
+        if (!rc) rc = fft_plan_get(b.V.npx, &b.fpx);
+        if (!rc) rc = fft_plan_get(b.V.npy, &b.fpy);
+        if (rc) {
+            fail(i, rc);
+            continue;
+        }
+        all.push_back(b);
+    }
+    const size_t cap = batch_cap_bytes();
+    for (int prec : {NUFDS_FP32, NUFDS_FP16_STORE, NUFDS_BF16_STORE}) {
+        std::vector<BatchView> wave;
+        size_t bytes = 0;
+        auto flush = [&]() {
+            if (wave.empty()) return;
+            int rc = run_wave(wave, prec, st, statuses);
+            if (rc)
+                for (auto &b : wave) fail(b.idx, rc);
+            wave.clear();
+            bytes = 0;
+        };
+        for (auto &b : all) {
+            if (b.P->prec != prec) continue;
+            size_t vb = view_batch_bytes(b, prec);
+            if (!wave.empty() && bytes + vb > cap) flush();
+            wave.push_back(b);
+            bytes += vb;
+        }
+        flush();
+    }
+    return first;
+}
+
 }  // namespace nufds
 
 extern "C" {
@@ -658,13 +1115,7 @@ int nufds_reconstruct(nufds_plan *P, const nufds_view *v, void *d_out, void *str
 int nufds_reconstruct_batch(nufds_plan *const *plans, const nufds_view *views,
                             void *const *d_outs, int32_t count, void *stream, int32_t *statuses) {
     if (count < 0 || (count > 0 && (!plans || !views || !d_outs))) return NUFDS_EINVAL;
-    int first = NUFDS_OK;
-    for (int32_t i = 0; i < count; ++i) {
-        int rc = reconstruct_impl(plans[i], &views[i], d_outs[i], (cudaStream_t)stream);
-        if (statuses) statuses[i] = rc;
-        if (rc && first == NUFDS_OK) first = rc;
-    }
-    return first;
+    return batch_impl(plans, views, d_outs, count, (cudaStream_t)stream, statuses);
 }
 
 void nufds_destroy(nufds_plan *P) {

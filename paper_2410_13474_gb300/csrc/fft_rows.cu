@@ -154,15 +154,7 @@ template <int R, bool INV> struct Dft {
 // ------------------------------------------------------------------------
 // passes
 // ------------------------------------------------------------------------
-struct PassArgs {
-    int L, npass, ncoarse;
-    int radix[kMaxPasses], stride[kMaxPasses];
-    uint32_t mag_stride[kMaxPasses];  // ceil(2^32 / stride), 0 for stride 1
-    uint32_t mag_radix[kMaxPasses];   // ceil(2^32 / radix)
-    const float2 *tw;                 // fine[64] | coarse[ncoarse]: W_L^q = coarse[q>>6] fine[q&63]
-    const float2 *mod1, *mod1_slot;   // e^{-i pi (n - L/2)/L}: natural / slot order
-    const float *pad_pre;             // (-1)^n / psi_hat(n - L/2), natural order
-};
+
 
 // exact n / d for n * d < 2^32 (host check in fft_plan_*); m == 0 means d == 1
 __device__ __forceinline__ uint32_t udiv(uint32_t n, uint32_t m) { return m ? __umulhi(n, m) : n; }
@@ -391,6 +383,36 @@ __global__ void __launch_bounds__(512) k_rows_pad2(PassArgs P, const TI *__restr
     }
 }
 
+// one row of the view pass: inverse DFT, chirp, the two half-grid forward DFTs
+template <class T>
+__device__ __forceinline__ void row_view_body(const PassArgs &P, const T *__restrict__ irow,
+                                              T *__restrict__ orow,
+                                              const float2 *__restrict__ chirp_slot,
+                                              float2 *__restrict__ scr, float2 *sm,
+                                              const float2 *tws, float inv, float sc) {
+    const int RL = P.radix[P.npass - 1];
+    // inverse DFT (DIF): natural -> slot order
+#define C_(R) dif_first_r<R, T>(P, irow, inv, sm, tws)
+    NUFDS_RADIX_SWITCH(P.radix[0], C_)
+#undef C_
+    __syncthreads();
+    for (int j = 1; j < P.npass - 1; ++j) {
+        mid_pass<true, false>(P, j, sm, tws);
+        __syncthreads();
+    }
+    // last inverse pass + chirp + first forward pass
+#define C_(R) fused_mid_r<R>(P, sm, chirp_slot, scr)
+    NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
+    __syncthreads();
+    forward_tail<T>(P, sm, tws, orow, sc, 0);
+#define C_(R) odd_first_r<R>(P, sm, scr)
+    NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
+    __syncthreads();
+    forward_tail<T>(P, sm, tws, orow, sc, 1);
+}
+
 template <class T>
 __global__ void __launch_bounds__(512) k_rows_view(PassArgs P, const T *__restrict__ in,
                                                    long in_ld,
@@ -402,30 +424,53 @@ __global__ void __launch_bounds__(512) k_rows_view(PassArgs P, const T *__restri
     const float2 *tws = load_tw(P, sm);
     const float inv = sc_in ? 1.0f / *sc_in : 1.0f, sc = sc_out ? *sc_out : 1.0f;
     float2 *scr = scratch + (long)blockIdx.x * P.L;
-    const int RL = P.radix[P.npass - 1];
-    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        const T *irow = in + (long)r * in_ld;
-        T *orow = out + (long)r * out_ld;
-        // inverse DFT (DIF): natural -> slot order
-#define C_(R) dif_first_r<R, T>(P, irow, inv, sm, tws)
-        NUFDS_RADIX_SWITCH(P.radix[0], C_)
-#undef C_
-        __syncthreads();
-        for (int j = 1; j < P.npass - 1; ++j) {
-            mid_pass<true, false>(P, j, sm, tws);
-            __syncthreads();
+    for (int r = blockIdx.x; r < rows; r += gridDim.x)
+        row_view_body<T>(P, in + (long)r * in_ld, out + (long)r * out_ld, chirp_slot, scr, sm, tws,
+                         inv, sc);
+}
+
+// Batched view pass over rows of many items (views, passes) of uneven length:
+// a persistent grid walks the flattened row list; the CTA reloads the pass
+// structure and twiddle tables when it moves to another item.
+template <class T>
+__global__ void __launch_bounds__(512) k_rows_view_batch(const PassArgs *__restrict__ args,
+                                                         const RowItem *__restrict__ items,
+                                                         const int *__restrict__ row_off,
+                                                         int nitems, float2 *__restrict__ scratch,
+                                                         int scr_stride) {
+    extern __shared__ float2 sm[];
+    __shared__ PassArgs sP;
+    __shared__ int s_item;
+    float2 *scr = scratch + (long)blockIdx.x * scr_stride;
+    const int total = row_off[nitems];
+    int cur = -1;
+    const float2 *tws = nullptr;
+    float inv = 1.0f, sc = 1.0f;
+    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = nitems - 1;  // last item with row_off <= g
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (row_off[mid] <= g) lo = mid;
+                else hi = mid - 1;
+            }
+            s_item = lo;
         }
-        // last inverse pass + chirp + first forward pass
-#define C_(R) fused_mid_r<R>(P, sm, chirp_slot, scr)
-        NUFDS_RADIX_SWITCH(RL, C_)
-#undef C_
         __syncthreads();
-        forward_tail<T>(P, sm, tws, orow, sc, 0);
-#define C_(R) odd_first_r<R>(P, sm, scr)
-        NUFDS_RADIX_SWITCH(RL, C_)
-#undef C_
+        const int it = s_item;
+        const RowItem &I = items[it];
+        if (it != cur) {
+            if (threadIdx.x == 0) sP = args[I.args];
+            __syncthreads();
+            tws = load_tw(sP, sm);
+            inv = I.sc_in ? 1.0f / *I.sc_in : 1.0f;
+            sc = I.sc_out ? *I.sc_out : 1.0f;
+            cur = it;
+        }
+        const int r = g - row_off[it];
+        row_view_body<T>(sP, (const T *)I.in + (long)r * I.in_ld, (T *)I.out + (long)r * I.out_ld,
+                         I.chirp, scr, sm, tws, inv, sc);
         __syncthreads();
-        forward_tail<T>(P, sm, tws, orow, sc, 1);
     }
 }
 
@@ -626,7 +671,7 @@ static int plan_host(int L, FftPlan &p, std::vector<float2> &f2, std::vector<dou
     p.threads = t < 64 ? 64 : (t > 512 ? 512 : t);
     p.ncoarse = (L + 63) / 64;
     p.smem_bytes = sizeof(float2) * (size_t)(host_phys(L) + 1 + 64 + p.ncoarse);
-    if (p.smem_bytes > 227 * 1024) return -3;
+    if (p.smem_bytes > 227 * 1024 - 1024) return -3;
     f2.assign(64 + p.ncoarse + 2 * (size_t)L, make_float2(0.f, 0.f));
     for (int j = 0; j < 64; ++j) {
         double a = -2.0 * M_PI * j / L;
@@ -673,6 +718,60 @@ static std::map<std::pair<int, int>, LenEntry *> g_cache;  // (device, L)
 
 static void set_smem_attrs(size_t bytes);
 
+static int grid_for(const void *fn, const FftPlan &p, int rows);
+
+// Autotuner of the row passes: time the view pass (the heaviest) with each
+// candidate block size on zeroed buffers and keep the fastest (per device and
+// length, once).  Falls back to the default on any failure.
+static void autotune_threads(FftPlan &p) {
+    const int L = p.L;
+    const int rows = std::min(256, 2 * L);
+    int cands[3] = {128, 256, 512}, best_t = p.threads;
+    float best = 1e30f;
+    float2 *in = nullptr, *out = nullptr, *scr = nullptr, *chirp = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const size_t nin = (size_t)rows * L, nout = 2 * nin;
+    bool ok = cudaMalloc(&in, nin * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&out, nout * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&chirp, (size_t)L * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&scr, (size_t)rows * L * sizeof(float2)) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    if (ok) {
+        cudaMemsetAsync(in, 0, nin * sizeof(float2), st);
+        cudaMemsetAsync(chirp, 0, (size_t)L * sizeof(float2), st);
+        const PassArgs a = fft_pass_args(p);
+        for (int t : cands) {
+            if (t < 64 || t > 512) continue;
+            FftPlan q = p;
+            q.threads = t;
+            const int grid = grid_for((const void *)k_rows_view<float2>, q, rows);
+            for (int rep = 0; rep < 4; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, st);
+                k_rows_view<float2><<<grid, t, p.smem_bytes, st>>>(a, in, L, chirp, out, 2 * L, rows,
+                                                                   scr, nullptr, nullptr);
+            }
+            cudaEventRecord(e1, st);
+            float ms = 0;
+            if (cudaEventSynchronize(e1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+                best = ms;
+                best_t = t;
+            }
+        }
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(chirp);
+    cudaFree(scr);
+    p.threads = best_t;
+}
+
 int fft_plan_get(int L, const FftPlan **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     int rc = init_constants();
@@ -707,6 +806,7 @@ int fft_plan_get(int L, const FftPlan **out) {
     cudaMemcpy(e->pad_pre, pad.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
     plan_point(e->plan, e->dev, e->deapod, e->pad_pre);
     set_smem_attrs(e->plan.smem_bytes);
+    autotune_threads(e->plan);
     g_cache[key] = e;
     *out = &e->plan;
     return 0;
@@ -743,7 +843,7 @@ int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pa
 
 size_t fft_tw_count(int L) { return 64 + (size_t)(L + 63) / 64 + 2 * (size_t)L; }
 
-static PassArgs pass_args(const FftPlan &p) {
+PassArgs fft_pass_args(const FftPlan &p) {
     PassArgs a;
     memset(&a, 0, sizeof a);
     a.L = p.L;
@@ -764,7 +864,7 @@ static PassArgs pass_args(const FftPlan &p) {
 
 static void set_smem_attrs(size_t bytes) {
     if (bytes > 48 * 1024) {
-        const int m = 227 * 1024;
+        const int m = 227 * 1024 - 1024;  // leave room for static shared memory
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
         cudaFuncSetAttribute(k_rows_pad2<float2, float2>, a, m);
         cudaFuncSetAttribute(k_rows_pad2<float2, __half2>, a, m);
@@ -774,6 +874,9 @@ static void set_smem_attrs(size_t bytes) {
         cudaFuncSetAttribute(k_rows_view<float2>, a, m);
         cudaFuncSetAttribute(k_rows_view<__half2>, a, m);
         cudaFuncSetAttribute(k_rows_view<__nv_bfloat162>, a, m);
+        cudaFuncSetAttribute(k_rows_view_batch<float2>, a, m);
+        cudaFuncSetAttribute(k_rows_view_batch<__half2>, a, m);
+        cudaFuncSetAttribute(k_rows_view_batch<__nv_bfloat162>, a, m);
     }
 }
 
@@ -796,7 +899,7 @@ int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, 
                      cudaStream_t st) {
     if (rows <= 0) return 0;
     const int grid = grid_for((const void *)k_rows_pad2<float2, float2>, p, rows);
-    const PassArgs a = pass_args(p);
+    const PassArgs a = fft_pass_args(p);
 #define L_(TI, TO)                                                                        \
     k_rows_pad2<TI, TO><<<grid, p.threads, p.smem_bytes, st>>>(a, (const TI *)in, in_ld,  \
                                                               (TO *)out, out_ld, rows,    \
@@ -816,7 +919,7 @@ int launch_rows_view(const FftPlan &p, const void *in, long in_ld, const float2 
                      long out_ld, int rows, float2 *scratch, int grid, int prec,
                      const float *sc_in, const float *sc_out, cudaStream_t st) {
     if (rows <= 0) return 0;
-    const PassArgs a = pass_args(p);
+    const PassArgs a = fft_pass_args(p);
 #define L_(T)                                                                               \
     k_rows_view<T><<<grid, p.threads, p.smem_bytes, st>>>(a, (const T *)in, in_ld, chirp,   \
                                                          (T *)out, out_ld, rows, scratch,   \
@@ -859,6 +962,75 @@ int launch_transpose(const void *in, long in_ld, void *out, long out_ld, int row
     else
         k_transpose<uint32_t><<<grid, dim3(32, 8), 0, st>>>((const uint32_t *)in, in_ld,
                                                             (uint32_t *)out, out_ld, rows, cols);
+    count_launch();
+    return check_launch();
+}
+
+int rows_view_batch_grid(int threads, size_t smem, int total_rows) {
+    int dev, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rows_view_batch<float2>, threads, smem);
+    if (per < 1) per = 1;
+    long g = (long)sms * per;
+    return (int)(g < total_rows ? g : total_rows);
+}
+
+int launch_rows_view_batch(const PassArgs *d_args, const RowItem *d_items, const int *d_row_off,
+                           int nitems, int total_rows, int threads, size_t smem, float2 *scratch,
+                           int scr_stride, int grid, int prec, cudaStream_t st) {
+    if (total_rows <= 0) return 0;
+#define L_(T)                                                                             \
+    k_rows_view_batch<T><<<grid, threads, smem, st>>>(d_args, d_items, d_row_off, nitems, \
+                                                      scratch, scr_stride)
+    if (prec == PREC_F32) L_(float2);
+    else if (prec == PREC_F16) L_(__half2);
+    else if (prec == PREC_BF16) L_(__nv_bfloat162);
+    else return -3;
+#undef L_
+    count_launch();
+    return check_launch();
+}
+
+template <class T>
+__global__ void k_transpose_batch(const TrItem *__restrict__ items, const int *__restrict__ off,
+                                  int nitems) {
+    __shared__ T tile[32][33];
+    __shared__ int s_item;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        int lo = 0, hi = nitems - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_item = lo;
+    }
+    __syncthreads();
+    const TrItem &I = items[s_item];
+    const int t = blockIdx.x - off[s_item];
+    const int c0 = (t % I.tiles_x) * 32, r0 = (t / I.tiles_x) * 32;
+    const T *in = (const T *)I.in;
+    T *out = (T *)I.out;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < I.rows && c < I.cols) tile[i][threadIdx.x] = in[(long)r * I.in_ld + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < I.rows && c < I.cols) out[(long)c * I.out_ld + r] = tile[threadIdx.x][i];
+    }
+}
+
+int launch_transpose_batch(const TrItem *d_items, const int *d_tile_off, int nitems,
+                           int total_tiles, int prec, cudaStream_t st) {
+    if (total_tiles <= 0) return 0;
+    if (prec_bytes(prec) == 8)
+        k_transpose_batch<float2><<<total_tiles, dim3(32, 8), 0, st>>>(d_items, d_tile_off, nitems);
+    else
+        k_transpose_batch<uint32_t><<<total_tiles, dim3(32, 8), 0, st>>>(d_items, d_tile_off,
+                                                                        nitems);
     count_launch();
     return check_launch();
 }

@@ -31,11 +31,11 @@ __device__ __forceinline__ int wrap(int m, int M) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
+__device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int by) {
     const T *G = (const T *)a.G;
     const float ginv = a.sc_g ? 1.0f / *a.sc_g : 1.0f, ssc = a.sc_s ? *a.sc_s : 1.0f;
-    const int jy = blockIdx.x * 32 + threadIdx.x;
-    const int jx = blockIdx.y * 8 + threadIdx.y;
+    const int jy = bx * 32 + threadIdx.x;
+    const int jx = by * 8 + threadIdx.y;
     const bool valid = jx < a.npx && jy < a.npy;
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
     float2 acc = make_float2(0.f, 0.f);
@@ -82,11 +82,35 @@ __global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
+__global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
+    stretch_body<T>(a, blockIdx.x, blockIdx.y);
+}
+
+__device__ __forceinline__ int find_item(const int *off, int nitems, int b) {
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_stretch_batch(const StretchArgs *__restrict__ items,
+                                                       const int *__restrict__ off, int nitems) {
+    const int it = find_item(off, nitems, blockIdx.x);
+    const StretchArgs &a = items[it];
+    const int t = blockIdx.x - off[it], tx = (a.npy + 31) / 32;
+    stretch_body<T>(a, t % tx, t / tx);
+}
+
+template <class T>
+__device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const T *Q = (const T *)a.Q;
     const float qinv = a.sc_q ? 1.0f / *a.sc_q : 1.0f;
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int i = bx * 32 + threadIdx.x;
+    const int j = by * 8 + threadIdx.y;
     if (i >= a.ox || j >= a.oy) return;
     const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
     const short2 b = a.rm_base[t];
@@ -135,11 +159,45 @@ __global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
     }
 }
 
+template <class T>
+__global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
+    remap_body<T>(a, blockIdx.x, blockIdx.y);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_remap_batch(const RemapArgs *__restrict__ items,
+                                                     const int *__restrict__ off, int nitems) {
+    const int it = find_item(off, nitems, blockIdx.x);
+    const RemapArgs &a = items[it];
+    const int t = blockIdx.x - off[it], tx = (a.ox + 31) / 32;
+    remap_body<T>(a, t % tx, t / tx);
+}
+
 int launch_stretch(const StretchArgs &a, cudaStream_t st) {
     dim3 grid((a.npy + 31) / 32, (a.npx + 7) / 8);
     if (a.prec == PREC_F32) k_stretch<float2><<<grid, dim3(32, 8), 0, st>>>(a);
     else if (a.prec == PREC_F16) k_stretch<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
     else k_stretch<__nv_bfloat162><<<grid, dim3(32, 8), 0, st>>>(a);
+    count_launch();
+    return check_launch();
+}
+
+int launch_stretch_batch(const StretchArgs *d_items, const int *d_off, int nitems, int total,
+                         int prec, cudaStream_t st) {
+    if (total <= 0) return 0;
+    if (prec == PREC_F32) k_stretch_batch<float2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
+    else if (prec == PREC_F16) k_stretch_batch<__half2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
+    else k_stretch_batch<__nv_bfloat162><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
+    count_launch();
+    return check_launch();
+}
+
+int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, int total, int prec,
+                       cudaStream_t st) {
+    if (total <= 0) return 0;
+    if (prec == PREC_F32) k_remap_batch<float2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
+    else if (prec == PREC_F16) k_remap_batch<__half2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
+    else k_remap_batch<__nv_bfloat162><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
     count_launch();
     return check_launch();
 }

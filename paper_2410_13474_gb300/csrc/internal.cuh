@@ -68,6 +68,42 @@ struct FftPlan {
     const float *pad_pre = nullptr;    // (-1)^n / psi_hat(n - L/2)
 };
 
+struct PassArgs {
+    int L, npass, ncoarse;
+    int radix[kMaxPasses], stride[kMaxPasses];
+    uint32_t mag_stride[kMaxPasses];  // ceil(2^32 / stride), 0 for stride 1
+    uint32_t mag_radix[kMaxPasses];   // ceil(2^32 / radix)
+    const float2 *tw;                 // fine[64] | coarse[ncoarse]: W_L^q = coarse[q>>6] fine[q&63]
+    const float2 *mod1, *mod1_slot;   // e^{-i pi (n - L/2)/L}: natural / slot order
+    const float *pad_pre;             // (-1)^n / psi_hat(n - L/2), natural order
+};
+
+// kernel arguments of plan p
+PassArgs fft_pass_args(const FftPlan &p);
+
+// Batched work: one item per (view, pass); rows [row_off[i], row_off[i+1]) of
+// a launch belong to item i.
+struct RowItem {
+    const void *in;
+    void *out;
+    const float2 *chirp;
+    long in_ld, out_ld;
+    int args;               // index into the PassArgs array
+    const float *sc_in, *sc_out;
+};
+struct TrItem {
+    const void *in;
+    void *out;
+    long in_ld, out_ld;
+    int rows, cols, tiles_x;
+};
+int launch_rows_view_batch(const PassArgs *d_args, const RowItem *d_items, const int *d_row_off,
+                           int nitems, int total_rows, int threads, size_t smem, float2 *scratch,
+                           int scr_stride, int grid, int prec, cudaStream_t st);
+int rows_view_batch_grid(int threads, size_t smem, int total_rows);
+int launch_transpose_batch(const TrItem *d_items, const int *d_tile_off, int nitems,
+                           int total_tiles, int prec, cudaStream_t st);
+
 // Natural index of a digit-reversed slot of plan p (host and device).
 __host__ __device__ inline int fft_index_of_slot(const FftPlan &p, int slot) {
     int n = 0;
@@ -147,6 +183,10 @@ struct StretchArgs {
     double *energy;         // if not null: += sum |S|^2 (before storage rounding)
 };
 int launch_stretch(const StretchArgs &a, cudaStream_t st);
+// batched: item i owns blocks [off[i], off[i+1]) of a 1-D grid (32 x 8 tiles)
+int launch_stretch_batch(const StretchArgs *d_items, const int *d_off, int nitems, int total,
+                         int prec, cudaStream_t st);
+inline int stretch_tiles(int npx, int npy) { return ((npy + 31) / 32) * ((npx + 7) / 8); }
 
 struct RemapArgs {
     const void *Q;          // oversampled FrT output, layout [my][mx], 2npy x 2npx
@@ -165,6 +205,9 @@ struct RemapArgs {
     const float *sc_q;
 };
 int launch_remap(const RemapArgs &a, cudaStream_t st);
+int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, int total, int prec,
+                       cudaStream_t st);
+inline int remap_tiles(int ox, int oy) { return ((ox + 31) / 32) * ((oy + 7) / 8); }
 
 // FP16 scales (device floats sc[]) from exact energy bounds (max |.| <= the
 // Frobenius norm, which Parseval gives for every DFT stage):

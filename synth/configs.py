@@ -69,3 +69,41 @@ UWA_16K = Workload("pointcloud-16384-532nm-0.307um-20000pt", 16384, LAMBDA_532, 
                    partial_views=16, partial_size=2048)
 
 ALL = {w.name: w for w in (SMALL_512, WA_4096, UWA_16K)}
+
+
+@dataclass(frozen=True)
+class BatchRequest:
+    holo: int          # index into the batch holograms
+    size: int          # view is size x size pixels at the full-view pitch of its z
+    dx: int            # view-centre offset from the full-view centre, in full-view pixels
+    dy: int
+    z: float
+
+
+def batch_workload(seed: int = 20241020, n_holo: int = 8, n_req: int = 64, lam: float = LAMBDA_532,
+                   sizes=(2048, 4096, 8192), view_sizes=(256, 512, 1024, 2048, 4096),
+                   z_range=(1.0e-3, 8.0e-3), max_fft: int = 24576):
+    """Holograms of seeded sizes and pitches, and partial-view requests of
+    uneven size, position and depth over them (the batched workload).  A
+    request's z is drawn in [max(z_min, z_chirp), z_max], where z_chirp keeps
+    the FFT size of the Fresnel stage within max_fft ((N pitch)^2/(lambda z)
+    <= max_fft)."""
+    rng = np.random.default_rng(seed)
+    holos = []
+    for i in range(n_holo):
+        n = int(rng.choice(sizes))
+        pitch = float(rng.uniform(0.3e-6, 0.5e-6))
+        npts = int(rng.integers(500, 5001))
+        holos.append(Workload("batch-holo-%d-%d" % (i, n), n, lam, pitch, npts, (1.0e-3, 8.0e-3),
+                              (0.5, 1.0), 4.0e-3, seed=seed * 100 + i))
+    reqs = []
+    for _ in range(n_req):
+        h = int(rng.integers(0, n_holo))
+        w = holos[h]
+        s = int(rng.choice([v for v in view_sizes if v <= w.n]))
+        lim = (w.n - s) // 2
+        dx, dy = (int(v) for v in rng.integers(-lim, lim + 1, size=2))
+        zc = (w.n * w.pitch) ** 2 / (lam * max_fft) * 1.02
+        z = float(rng.uniform(max(z_range[0], zc), z_range[1]))
+        reqs.append(BatchRequest(h, s, dx, dy, z))
+    return holos, reqs
