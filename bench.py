@@ -421,6 +421,82 @@ def run_batch(args):
         pl.close()
 
 
+def run_serve(args):
+    """Serving workload: resident holograms, a seeded Poisson stream of view
+    requests, continuous batching on two streams under an HBM budget; against
+    the same stream served one request at a time with the plain single-view
+    call; plus a saturation sweep of the offered load."""
+    import torch
+
+    import paper_2410_13474_gb300 as nf
+    import synth
+    from paper_2410_13474_gb300.serving import GpuExecutor, Request, Scheduler
+    from synth.configs import serve_workload
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2410_13474_gb300 import build as b
+    b.build()
+    nreq = args.requests
+    holos, breqs, t_arr = serve_workload(n_req=nreq)
+    t0 = time.time()
+    plans = []
+    for w in holos:
+        h = synth.gpu_hologram(w.point_cloud(), w.wavelength, w.pitch, w.n, w.n)
+        plans.append(nf.Plan(w.wavelength, w.pitch, w.n, w.n, h))
+        del h
+    torch.cuda.synchronize()
+    init_s = time.time() - t0
+    resident = sum(p.device_bytes() for p in plans)
+    budget = 120 * 10 ** 9
+    views = []
+    for br in breqs:
+        pl = plans[br.holo]
+        p = pl.view_plan(nf.View(z=br.z))["pitch_out_x_m"]
+        views.append(nf.View(z=br.z, center_x=br.dx * p, center_y=br.dy * p, width=br.size * p,
+                             height=br.size * p, out_nx=br.size, out_ny=br.size))
+    ws = [int(plans[br.holo].view_plan(v)["workspace_bytes"]) for br, v in zip(breqs, views)]
+    pix = [br.size * br.size for br in breqs]
+
+    def make(scale=1.0, count=None):
+        m = len(breqs) if count is None else count
+        return [Request(i, breqs[i].holo, views[i], float(t_arr[i]) / scale, ws_bytes=ws[i])
+                for i in range(m)]
+
+    def serve(reqs, single):
+        slots = 1 if single else 2
+        ex = GpuExecutor(plans, slots=slots, single=single)
+        sched = Scheduler(ex, budget_bytes=budget - resident, slots=slots,
+                          max_batch=1 if single else 16)
+        torch.cuda.synchronize()
+        st = sched.run(reqs)
+        torch.cuda.synchronize()
+        d = st.as_dict()
+        d["Mpix_per_s"] = round(sum(pix[r.rid] for r in reqs if r.t_done) / st.wall_s / 1e6, 2)
+        return d
+
+    # warm both paths (tables, graphs, autotuner) on a short prefix
+    serve(make(count=min(64, nreq)), False)
+    serve(make(count=min(16, nreq)), True)
+    served = serve(make(), False)
+    single = serve(make(), True)
+    sweep = []
+    for mult in (2.0, 5.0):
+        m = min(nreq, max(200, nreq // 5))
+        sweep.append({"offered_rate": args.rate * mult, "requests": m,
+                      "batched": serve(make(mult, m), False), "one_at_a_time": serve(make(mult, m), True)})
+    line = {"metric": "served views/s with p50/p99 latency (continuous batching)",
+            "value": served["throughput"], "unit": "views/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve-%d-requests-%d-holograms" % (nreq, len(holos)),
+                       "rate_per_s": args.rate, "holograms": [[w.n, round(w.pitch * 1e6, 4)] for w in holos],
+                       "hbm_budget_bytes": budget, "resident_bytes": resident, "slots": 2,
+                       "max_batch": 16},
+            "served": served, "one_at_a_time": single, "sweep": sweep, "init_s": round(init_s, 1)}
+    print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,11 +504,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uwa16k",
-                    choices=["uwa16k", "wa4096", "small512", "batch64"])
+                    choices=["uwa16k", "wa4096", "small512", "batch64", "serve"])
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     w = _workload(args.workload)
     if args.impl == "reference":
         run_reference(args, w)

@@ -129,7 +129,13 @@ int nufds_view_plan(const nufds_params *params, const nufds_view *view, nufds_vi
 int nufds_reconstruct(nufds_plan *plan, const nufds_view *view, void *d_out, void *cuda_stream);
 
 /*
- * Reconstruct count views, each of its own plan, in order on cuda_stream.
+ * Reconstruct count views, each of its own plan (plans may repeat, sizes may
+ * differ), on cuda_stream.  Views are grouped into waves whose working memory
+ * fits a cap (environment variable NUFDS_BATCH_WS_GB, default 48); each wave
+ * runs as one CUDA graph: per-view tables, then one persistent launch per
+ * stage over all views.  Results are bitwise those of nufds_reconstruct.
+ * The batch workspace is kept per (device, stream), so batches on different
+ * streams may run concurrently (their plans' spectra are only read).
  * statuses (may be NULL) receives one code per view; a failing view does not
  * stop the others.  Returns NUFDS_OK if every view succeeded, else the first
  * error code.

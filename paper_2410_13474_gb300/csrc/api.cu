@@ -180,14 +180,17 @@ static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
     o->z = z;
     o->cx = v->center_x_m;
     o->cy = v->center_y_m;
+    // Extremes of the Eq. 17 image over the boundary pixels.  With u = x/R,
+    // v = y/R: u / sqrt(1 - v^2) = x / sqrt(x^2 + z^2) does not depend on y, so
+    // k_x = N pitch (1 - v^2)^(1/4) g(x / sqrt(x^2 + z^2)) / lambda falls in
+    // magnitude with |y| along a vertical edge and grows with x along a
+    // horizontal one (and x <-> y for k_y).  The extremes over the boundary are
+    // therefore at the corners or at the edge pixels nearest the axes; those
+    // candidates give the same min/max as evaluating every boundary pixel.
     double kmin[2] = {1e300, 1e300}, kmax[2] = {-1e300, -1e300};
-    const long nb = 2L * ox + 2L * oy;
-    for (long t = 0; t < nb; ++t) {
-        int i, j;
-        if (t < ox) { i = (int)t; j = 0; }
-        else if (t < 2L * ox) { i = (int)(t - ox); j = oy - 1; }
-        else if (t < 2L * ox + oy) { i = 0; j = (int)(t - 2L * ox); }
-        else { i = ox - 1; j = (int)(t - 2L * ox - oy); }
+    auto eval = [&](int i, int j) {
+        i = i < 0 ? 0 : (i >= ox ? ox - 1 : i);
+        j = j < 0 ? 0 : (j >= oy ? oy - 1 : j);
         double xo = o->cx + (i - 0.5 * ox) * o->px, yo = o->cy + (j - 0.5 * oy) * o->py;
         double R0 = sqrt(xo * xo + yo * yo + z * z);
         double up, vp;
@@ -197,7 +200,19 @@ static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
         kmax[0] = fmax(kmax[0], kx);
         kmin[1] = fmin(kmin[1], ky);
         kmax[1] = fmax(kmax[1], ky);
+    };
+    // pixel index nearest the axis: x_o = c + (i - n/2) p = 0
+    const int ia = (int)floor(0.5 * ox - o->cx / o->px), ja = (int)floor(0.5 * oy - o->cy / o->py);
+    for (int d = -1; d <= 2; ++d) {
+        eval(0, ja + d);
+        eval(ox - 1, ja + d);
+        eval(ia + d, 0);
+        eval(ia + d, oy - 1);
     }
+    eval(0, 0);
+    eval(ox - 1, 0);
+    eval(0, oy - 1);
+    eval(ox - 1, oy - 1);
     o->klo_x = (long)floor(kmin[0]);
     o->khi_x = (long)ceil(kmax[0]);
     o->klo_y = (long)floor(kmin[1]);
@@ -562,7 +577,7 @@ struct BatchWs {
     cudaStream_t cap = nullptr;  // private stream the graphs are captured on
 };
 static std::mutex g_batch_mu;
-static std::map<int, BatchWs *> g_batch;
+static std::map<std::pair<int, cudaStream_t>, BatchWs *> g_batch;  // per (device, stream)
 
 static size_t batch_cap_bytes() {
     const char *e = getenv("NUFDS_BATCH_WS_GB");
@@ -621,8 +636,9 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
     BatchWs *B;
     {
         std::lock_guard<std::mutex> lk(g_batch_mu);
-        B = g_batch[dev];
-        if (!B) B = g_batch[dev] = new BatchWs();
+        BatchWs *&slot_ws = g_batch[std::make_pair(dev, st)];
+        if (!slot_ws) slot_ws = new BatchWs();
+        B = slot_ws;
     }
     if (need > B->bytes) {
         cudaStreamSynchronize(st);

@@ -107,3 +107,38 @@ def batch_workload(seed: int = 20241020, n_holo: int = 8, n_req: int = 64, lam: 
         z = float(rng.uniform(max(z_range[0], zc), z_range[1]))
         reqs.append(BatchRequest(h, s, dx, dy, z))
     return holos, reqs
+
+
+def serve_workload(seed: int = 20241021, n_holo: int = 12, n_req: int = 10000, rate: float = 200.0,
+                   lam: float = LAMBDA_532, sizes=(2048, 4096, 8192, 16384),
+                   view_sizes=(256, 512, 1024, 2048, 4096), max_fft: int = 24576,
+                   resident_cap_bytes: float = 72e9):
+    """Resident holograms and a seeded Poisson stream of view requests (the
+    serving workload).  Hologram sizes are drawn from `sizes` until the
+    resident set (spectrum 32 N^2 B plus tables ~30 N^2 B each) would pass
+    resident_cap_bytes; then the smallest size is used.  A request's z is drawn
+    in [max(2 mm, z_chirp), 10 mm] (z_chirp keeps the Fresnel-stage FFT within
+    max_fft).  Returns (holograms, requests, arrival_times)."""
+    rng = np.random.default_rng(seed)
+    holos, resident = [], 0.0
+    for i in range(n_holo):
+        n = int(rng.choice(sizes))
+        if resident + 62.0 * n * n > resident_cap_bytes:
+            n = min(sizes)
+        resident += 62.0 * n * n
+        pitch = float(rng.uniform(0.307e-6, 0.5e-6))
+        npts = int(rng.integers(500, 5001))
+        holos.append(Workload("serve-holo-%d-%d" % (i, n), n, lam, pitch, npts, (2.0e-3, 10.0e-3),
+                              (0.5, 1.0), 6.0e-3, seed=seed * 100 + i))
+    reqs = []
+    for _ in range(n_req):
+        h = int(rng.integers(0, n_holo))
+        w = holos[h]
+        s = int(rng.choice([v for v in view_sizes if v <= w.n]))
+        lim = (w.n - s) // 2
+        dx, dy = (int(v) for v in rng.integers(-lim, lim + 1, size=2))
+        zc = (w.n * w.pitch) ** 2 / (lam * max_fft) * 1.02
+        z = float(rng.uniform(max(2.0e-3, zc), 10.0e-3))
+        reqs.append(BatchRequest(h, s, dx, dy, z))
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    return holos, reqs, t

@@ -83,3 +83,24 @@ def test_full_view_is_on_its_own_lattice(built):
     assert nf.view_plan(532e-9, 0.4e-6, 512, 512, sub)["on_full_view_lattice"] == 1
     off = nf.View(z=1e-3, center_x=0.3 * p, width=64 * p, height=64 * p, out_nx=64, out_ny=64)
     assert nf.view_plan(532e-9, 0.4e-6, 512, 512, off)["on_full_view_lattice"] == 0
+
+
+def test_planner_matches_oracle_random_views(built):
+    """The library evaluates Eq. 17 only at the corners and at the edge pixels
+    nearest the axes; the oracle scans every boundary pixel.  Same integers."""
+    rng = np.random.default_rng(1)
+    for it in range(150):
+        n = int(rng.choice([256, 512, 1024, 2048]))
+        lam, pitch = 532e-9, float(rng.uniform(0.3e-6, 0.5e-6))
+        z = float(rng.uniform(0.5e-3, 5e-3))
+        B = oracle.plan_view(lam, pitch, n, n, z)["width"]
+        p = B / n * (float(rng.uniform(0.5, 1.5)) if it % 5 == 0 else 1.0)
+        ox, oy = int(rng.integers(8, n)), int(rng.integers(8, n))
+        cx = 0.0 if it % 3 == 0 else float(rng.uniform(-0.5, 0.5)) * (B - ox * p)
+        cy = float(rng.uniform(-0.5, 0.5)) * (B - oy * p)
+        v = nf.View(z=z, center_x=cx, center_y=cy, width=ox * p, height=oy * p, out_nx=ox,
+                    out_ny=oy)
+        got = nf.view_plan(lam, pitch, n, n, v)
+        ref = oracle.plan_view(lam, pitch, n, n, z, cx, cy, ox * p, oy * p, ox, oy)
+        for k in ["k_lo_x", "k_hi_x", "k_lo_y", "k_hi_y", "np_x", "np_y"]:
+            assert got[k] == ref[k], (it, k)
