@@ -210,7 +210,7 @@ __device__ __forceinline__ void dif_first_r(const PassArgs &P, const TI *__restr
     for (int o = threadIdx.x; o < s; o += blockDim.x) {
         float2 x[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) x[i] = ld_c(irow, o + i * s, inv);
+        for (int i = 0; i < R; ++i) x[i] = ld_cs(irow, o + i * s, inv);
         Dft<R, true>::run(x);
         if (o) {
             float2 W[R];
@@ -274,7 +274,7 @@ __device__ __forceinline__ void pad_first_r(const PassArgs &P, const TI *__restr
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int m = n + i * nb;
-            float2 v = cscale(ld_c(irow, m, inv), __ldg(P.pad_pre + m));
+            float2 v = cscale(ld_cs(irow, m, inv), __ldg(P.pad_pre + m));
             x[i] = a ? cmul(v, __ldg(P.mod1 + m)) : v;
         }
         Dft<R, false>::run(x);
@@ -291,7 +291,8 @@ __device__ __forceinline__ void pad_first_r(const PassArgs &P, const TI *__restr
     }
 }
 
-// pass 0 of the forward DIT: shared -> global, out[2k + a] = (-1)^k X[k]
+// pass 0 of the forward DIT: shared -> global, fine index 2k + a = (-1)^k X[k],
+// stored in the plane layout at a L + k
 template <int R, class TO>
 __device__ __forceinline__ void dit_last_r(const PassArgs &P, const float2 *sm, const float2 *tws,
                                            TO *__restrict__ orow, float sc, int a) {
@@ -312,7 +313,7 @@ __device__ __forceinline__ void dit_last_r(const PassArgs &P, const float2 *sm, 
             const int f = o + k * s;
             float2 v = x[k];
             if (f & 1) v = make_float2(-v.x, -v.y);
-            st_c(orow, 2 * f + a, v, sc);
+            st_cs(orow, a * P.L + f, v, sc);
         }
     }
 }

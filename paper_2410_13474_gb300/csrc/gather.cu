@@ -12,6 +12,8 @@
 //
 // Both read a coordinate table (integer fine-grid base + FP32 fraction,
 // derived in FP64) and wrap indices periodically (the DTFT is periodic).
+// The 2x grids are stored plane-wise per axis (fine index m at
+// (m & 1) * L + m / 2), as the row passes write them.
 #include <math.h>
 
 #include "internal.cuh"
@@ -54,10 +56,10 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
             const int mx0 = b.x - kW / 2 + 1 + a.Nx, my0 = b.y - kW / 2 + 1 + a.Ny;
             int cols[kW];
 #pragma unroll
-            for (int j = 0; j < kW; ++j) cols[j] = wrap(my0 + j, My);
+            for (int j = 0; j < kW; ++j) cols[j] = fine_pos(wrap(my0 + j, My), a.Ny);
 #pragma unroll
             for (int i = 0; i < kW; ++i) {
-                const long row = (long)wrap(mx0 + i, Mx) * My;
+                const long row = (long)fine_pos(wrap(mx0 + i, Mx), a.Nx) * My;
                 float2 r = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < kW; ++j) {
@@ -126,11 +128,11 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const int my0 = (int)(b.y - 2 * a.kc_y) + a.npy - kW / 2 + 1;
     int cols[kW];
 #pragma unroll
-    for (int q = 0; q < kW; ++q) cols[q] = wrap(mx0 + q, Mx);
+    for (int q = 0; q < kW; ++q) cols[q] = fine_pos(wrap(mx0 + q, Mx), a.npx);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < kW; ++p) {
-        const long row = (long)wrap(my0 + p, My) * Mx;
+        const long row = (long)fine_pos(wrap(my0 + p, My), a.npy) * Mx;
         float2 r = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < kW; ++q) {

@@ -32,6 +32,26 @@ __device__ __forceinline__ float2 ld_c(const __half2 *p, long i, float inv) {
 __device__ __forceinline__ float2 ld_c(const __nv_bfloat162 *p, long i, float) {
     return __bfloat1622float2(__ldg(p + i));
 }
+// streaming variants: data read or written once (keep L2 for reused data)
+__device__ __forceinline__ float2 ld_cs(const float2 *p, long i, float) { return __ldcs(p + i); }
+__device__ __forceinline__ float2 ld_cs(const __half2 *p, long i, float inv) {
+    float2 v = __half22float2(__ldcs(p + i));
+    return make_float2(v.x * inv, v.y * inv);
+}
+__device__ __forceinline__ float2 ld_cs(const __nv_bfloat162 *p, long i, float) {
+    return __bfloat1622float2(__ldcs(p + i));
+}
+__device__ __forceinline__ void st_cs(float2 *p, long i, float2 v, float) { __stcs(p + i, v); }
+__device__ __forceinline__ void st_cs(__half2 *p, long i, float2 v, float sc) {
+    __stcs(p + i, __float22half2_rn(make_float2(v.x * sc, v.y * sc)));
+}
+__device__ __forceinline__ void st_cs(__nv_bfloat162 *p, long i, float2 v, float) {
+    __stcs(p + i, __float22bfloat162_rn(v));
+}
+// A row on the 2x grid is stored as two planes: fine index m = 2k + a sits at
+// a * L + k (L = unpadded length), so each half is written contiguously.
+__device__ __forceinline__ int fine_pos(int m, int L) { return (m & 1) * L + (m >> 1); }
+
 __device__ __forceinline__ void st_c(float2 *p, long i, float2 v, float) { p[i] = v; }
 __device__ __forceinline__ void st_c(__half2 *p, long i, float2 v, float sc) {
     p[i] = __float22half2_rn(make_float2(v.x * sc, v.y * sc));
@@ -120,8 +140,8 @@ int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pa
                   cudaStream_t st);
 
 // Padded forward pass: rows of length L (in, row stride in_ld elements) ->
-// rows of length 2L (out, row stride out_ld):
-//   out[r][2k + a] = (-1)^k sum_n in[r][n] pre[n] e^{-i pi a (n - L/2)/L} e^{-2 pi i n k/L}
+// rows of length 2L (out, row stride out_ld), fine index 2k + a stored at a L + k:
+//   out[r][a L + k] = (-1)^k sum_n in[r][n] pre[n] e^{-i pi a (n - L/2)/L} e^{-2 pi i n k/L}
 // with pre = pad_pre.  This is the centred DFT on the 2x oversampled grid of
 // the deapodised row.
 // in_prec: storage of in (PREC_F32 for the hologram); out: storage prec.
