@@ -15,21 +15,90 @@
 // The 2x grids are stored plane-wise per axis (fine index m at
 // (m & 1) * L + m / 2), as the row passes write them.
 #include <math.h>
+#include <stdlib.h>
+
+#include <map>
+#include <mutex>
 
 #include "internal.cuh"
 
 namespace nufds {
 
-__device__ __forceinline__ float es_weight(float d) {
-    // psi(d) = exp(beta (sqrt(1 - (2d/W)^2) - 1)), 0 outside |d| <= W/2
-    float t = d * (2.0f / kW);
-    float q = 1.0f - t * t;
-    return q > 0.0f ? expf((float)kBeta * (sqrtf(q) - 1.0f)) : 0.0f;
+// Kernel weights of the kW taps for a fractional offset f in [0, 1): tap i is
+// at distance d_i = f + kW/2 - 1 - i and weighs psi(d_i) =
+// exp(beta (sqrt(1 - (2 d_i / kW)^2) - 1)).  Each psi(f + c_i) is smooth in f,
+// so it is evaluated as a degree-kEsDeg polynomial in t = 2f - 1 whose
+// coefficients are Chebyshev interpolants built in FP64 on the host (max
+// error ~1e-7 absolute, weights <= 1).
+constexpr int kEsDeg = 12;
+__constant__ float c_es[kW][kEsDeg + 1];
+
+__device__ __forceinline__ void es_weights(float f, float *w) {
+    const float t = 2.0f * f - 1.0f;
+#pragma unroll
+    for (int i = 0; i < kW; ++i) {
+        float p = c_es[i][kEsDeg];
+#pragma unroll
+        for (int k = kEsDeg - 1; k >= 0; --k) p = fmaf(p, t, c_es[i][k]);
+        w[i] = p;
+    }
 }
 
+static double psi_host(double d) {
+    const double u = 2.0 * d / kW, q = 1.0 - u * u;
+    return q > 0.0 ? exp(kBeta * (sqrt(q) - 1.0)) : 0.0;
+}
+
+// Chebyshev interpolation of each tap's weight on kEsDeg + 1 nodes, converted
+// to monomial coefficients in t; uploaded once per device.
+static int es_init() {
+    static std::mutex mu;
+    static std::map<int, bool> ready;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -4;
+    std::lock_guard<std::mutex> lk(mu);
+    if (ready[dev]) return 0;
+    const int n = kEsDeg + 1;
+    float h[kW][kEsDeg + 1];
+    for (int i = 0; i < kW; ++i) {
+        double a[kEsDeg + 1] = {0};
+        for (int k = 0; k < n; ++k) {
+            double s = 0;
+            for (int j = 0; j < n; ++j) {
+                const double x = cos(M_PI * (j + 0.5) / n);
+                s += psi_host(0.5 * (x + 1.0) + (kW / 2 - 1 - i)) * cos(k * M_PI * (j + 0.5) / n);
+            }
+            a[k] = 2.0 * s / n;
+        }
+        a[0] *= 0.5;
+        // sum a_k T_k(t) -> monomials, T_{k+1} = 2 t T_k - T_{k-1}
+        double mono[kEsDeg + 1] = {0}, tk[kEsDeg + 1] = {0}, tkm1[kEsDeg + 1] = {0};
+        tkm1[0] = 1.0;  // T_0
+        tk[1] = 1.0;    // T_1
+        mono[0] += a[0];
+        if (kEsDeg >= 1) mono[1] += a[1];
+        for (int k = 2; k <= kEsDeg; ++k) {
+            double nx[kEsDeg + 1] = {0};
+            for (int m = 0; m <= kEsDeg; ++m) {
+                if (m >= 1) nx[m] += 2.0 * tk[m - 1];
+                nx[m] -= tkm1[m];
+            }
+            for (int m = 0; m <= kEsDeg; ++m) {
+                tkm1[m] = tk[m];
+                tk[m] = nx[m];
+                mono[m] += a[k] * nx[m];
+            }
+        }
+        for (int m = 0; m <= kEsDeg; ++m) h[i][m] = (float)mono[m];
+    }
+    if (cudaMemcpyToSymbol(c_es, h, sizeof(h)) != cudaSuccess) return -4;
+    ready[dev] = true;
+    return 0;
+}
+
+// m in [-M, 2M): periodic index without integer division
 __device__ __forceinline__ int wrap(int m, int M) {
-    m %= M;
-    return m < 0 ? m + M : m;
+    return m < 0 ? m + M : (m >= M ? m - M : m);
 }
 
 template <class T>
@@ -38,44 +107,50 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
     const float ginv = a.sc_g ? 1.0f / *a.sc_g : 1.0f, ssc = a.sc_s ? *a.sc_s : 1.0f;
     const int jy = bx * 32 + threadIdx.x;
     const int jx = by * 8 + threadIdx.y;
-    const bool valid = jx < a.npx && jy < a.npy;
+    const bool inside = jx < a.npx && jy < a.npy;
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
-    float2 acc = make_float2(0.f, 0.f);
-    if (valid && kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
+    bool valid = false;
+    short2 b = make_short2(0, 0);
+    float2 f = make_float2(0.f, 0.f);
+    if (inside && kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
         const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
-        const short2 b = a.pb_base[t];
+        b = a.pb_base[t];
         if (b.x != kMasked) {
-            const float2 f = a.pb_frac[t];
-            const int Mx = 2 * a.Nx, My = 2 * a.Ny;
-            float wx[kW], wy[kW];
-#pragma unroll
-            for (int i = 0; i < kW; ++i) {
-                wx[i] = es_weight(f.x + (kW / 2 - 1 - i));
-                wy[i] = es_weight(f.y + (kW / 2 - 1 - i));
-            }
-            const int mx0 = b.x - kW / 2 + 1 + a.Nx, my0 = b.y - kW / 2 + 1 + a.Ny;
+            f = a.pb_frac[t];
+            valid = true;
+        }
+    }
+    const int Mx = 2 * a.Nx, My = 2 * a.Ny;
+    // first taps on the fine grid, unwrapped (rows = x, columns = y)
+    const int r0 = b.x - kW / 2 + 1 + a.Nx, c0 = b.y - kW / 2 + 1 + a.Ny;
+    float2 acc = make_float2(0.f, 0.f);
+    if (valid) {
+        float wx[kW], wy[kW];
+        es_weights(f.x, wx);
+        es_weights(f.y, wy);
+        {
             int cols[kW];
 #pragma unroll
-            for (int j = 0; j < kW; ++j) cols[j] = fine_pos(wrap(my0 + j, My), a.Ny);
+            for (int j = 0; j < kW; ++j) cols[j] = fine_pos(wrap(c0 + j, My), a.Ny);
 #pragma unroll
             for (int i = 0; i < kW; ++i) {
-                const long row = (long)fine_pos(wrap(mx0 + i, Mx), a.Nx) * My;
+                const long row = (long)fine_pos(wrap(r0 + i, Mx), a.Nx) * My;
                 float2 r = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < kW; ++j) {
-                    float2 g = ld_c(G, row + cols[j], 1.0f);
-                    r.x = fmaf(wy[j], g.x, r.x);
-                    r.y = fmaf(wy[j], g.y, r.y);
+                    float2 gv = ld_c(G, row + cols[j], 1.0f);
+                    r.x = fmaf(wy[j], gv.x, r.x);
+                    r.y = fmaf(wy[j], gv.y, r.y);
                 }
                 acc.x = fmaf(wx[i], r.x, acc.x);
                 acc.y = fmaf(wx[i], r.y, acc.y);
             }
-            // (-1)^(jx + jy): centring of the inverse transforms that follow
-            if ((jx + jy) & 1) acc = make_float2(-acc.x, -acc.y);
-            acc = make_float2(acc.x * ginv, acc.y * ginv);
         }
+        // (-1)^(jx + jy): centring of the inverse transforms that follow
+        if ((jx + jy) & 1) acc = make_float2(-acc.x, -acc.y);
+        acc = make_float2(acc.x * ginv, acc.y * ginv);
     }
-    if (valid) st_c((T *)a.S, (long)jx * a.npy + jy, acc, ssc);
+    if (inside) st_c((T *)a.S, (long)jx * a.npy + jy, acc, ssc);
     if (a.energy) {  // uniform over the launch; every lane reaches the shuffles
         double e = (double)acc.x * acc.x + (double)acc.y * acc.y;
         for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -84,7 +159,7 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_stretch(StretchArgs a) {
+__global__ void __launch_bounds__(256, 4) k_stretch(StretchArgs a) {
     stretch_body<T>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -99,7 +174,7 @@ __device__ __forceinline__ int find_item(const int *off, int nitems, int b) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_stretch_batch(const StretchArgs *__restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_stretch_batch(const StretchArgs *__restrict__ items,
                                                        const int *__restrict__ off, int nitems) {
     const int it = find_item(off, nitems, blockIdx.x);
     const StretchArgs &a = items[it];
@@ -113,35 +188,40 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const float qinv = a.sc_q ? 1.0f / *a.sc_q : 1.0f;
     const int i = bx * 32 + threadIdx.x;
     const int j = by * 8 + threadIdx.y;
-    if (i >= a.ox || j >= a.oy) return;
-    const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
-    const short2 b = a.rm_base[t];
-    const float2 f = a.rm_frac[t];
-    const int Mx = 2 * a.npx, My = 2 * a.npy;
-    float wx[kW], wy[kW];
-#pragma unroll
-    for (int q = 0; q < kW; ++q) {
-        wx[q] = es_weight(f.x + (kW / 2 - 1 - q));
-        wy[q] = es_weight(f.y + (kW / 2 - 1 - q));
+    const bool valid = i < a.ox && j < a.oy;
+    short2 b = make_short2(0, 0);
+    float2 f = make_float2(0.f, 0.f);
+    if (valid) {
+        const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
+        b = a.rm_base[t];
+        f = a.rm_frac[t];
     }
-    const int mx0 = (int)(b.x - 2 * a.kc_x) + a.npx - kW / 2 + 1;
-    const int my0 = (int)(b.y - 2 * a.kc_y) + a.npy - kW / 2 + 1;
-    int cols[kW];
-#pragma unroll
-    for (int q = 0; q < kW; ++q) cols[q] = fine_pos(wrap(mx0 + q, Mx), a.npx);
+    const int Mx = 2 * a.npx, My = 2 * a.npy;
+    // first taps on the fine grid, unwrapped (rows = y, columns = x)
+    const int c0 = (int)(b.x - 2 * a.kc_x) + a.npx - kW / 2 + 1;
+    const int r0 = (int)(b.y - 2 * a.kc_y) + a.npy - kW / 2 + 1;
     float2 acc = make_float2(0.f, 0.f);
+    if (!valid) return;
+    float wx[kW], wy[kW];
+    es_weights(f.x, wx);
+    es_weights(f.y, wy);
+    {
+        int cols[kW];
 #pragma unroll
-    for (int p = 0; p < kW; ++p) {
-        const long row = (long)fine_pos(wrap(my0 + p, My), a.npy) * Mx;
-        float2 r = make_float2(0.f, 0.f);
+        for (int q = 0; q < kW; ++q) cols[q] = fine_pos(wrap(c0 + q, Mx), a.npx);
 #pragma unroll
-        for (int q = 0; q < kW; ++q) {
-            float2 g = ld_c(Q, row + cols[q], 1.0f);
-            r.x = fmaf(wx[q], g.x, r.x);
-            r.y = fmaf(wx[q], g.y, r.y);
+        for (int p = 0; p < kW; ++p) {
+            const long row = (long)fine_pos(wrap(r0 + p, My), a.npy) * Mx;
+            float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < kW; ++q) {
+                float2 g = ld_c(Q, row + cols[q], 1.0f);
+                r.x = fmaf(wx[q], g.x, r.x);
+                r.y = fmaf(wx[q], g.y, r.y);
+            }
+            acc.x = fmaf(wy[p], r.x, acc.x);
+            acc.y = fmaf(wy[p], r.y, acc.y);
         }
-        acc.x = fmaf(wy[p], r.x, acc.x);
-        acc.y = fmaf(wy[p], r.y, acc.y);
     }
     acc = make_float2(acc.x * qinv, acc.y * qinv);
     const long o = (long)j * a.ox + i;
@@ -162,12 +242,12 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_remap(RemapArgs a) {
+__global__ void __launch_bounds__(256, 4) k_remap(RemapArgs a) {
     remap_body<T>(a, blockIdx.x, blockIdx.y);
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_remap_batch(const RemapArgs *__restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_remap_batch(const RemapArgs *__restrict__ items,
                                                      const int *__restrict__ off, int nitems) {
     const int it = find_item(off, nitems, blockIdx.x);
     const RemapArgs &a = items[it];
@@ -176,6 +256,7 @@ __global__ void __launch_bounds__(256) k_remap_batch(const RemapArgs *__restrict
 }
 
 int launch_stretch(const StretchArgs &a, cudaStream_t st) {
+    if (es_init()) return -4;
     dim3 grid((a.npy + 31) / 32, (a.npx + 7) / 8);
     if (a.prec == PREC_F32) k_stretch<float2><<<grid, dim3(32, 8), 0, st>>>(a);
     else if (a.prec == PREC_F16) k_stretch<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
@@ -186,6 +267,7 @@ int launch_stretch(const StretchArgs &a, cudaStream_t st) {
 
 int launch_stretch_batch(const StretchArgs *d_items, const int *d_off, int nitems, int total,
                          int prec, cudaStream_t st) {
+    if (es_init()) return -4;
     if (total <= 0) return 0;
     if (prec == PREC_F32) k_stretch_batch<float2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
     else if (prec == PREC_F16) k_stretch_batch<__half2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
@@ -196,6 +278,7 @@ int launch_stretch_batch(const StretchArgs *d_items, const int *d_off, int nitem
 
 int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, int total, int prec,
                        cudaStream_t st) {
+    if (es_init()) return -4;
     if (total <= 0) return 0;
     if (prec == PREC_F32) k_remap_batch<float2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
     else if (prec == PREC_F16) k_remap_batch<__half2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
@@ -205,6 +288,7 @@ int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, i
 }
 
 int launch_remap(const RemapArgs &a, cudaStream_t st) {
+    if (es_init()) return -4;
     dim3 grid((a.ox + 31) / 32, (a.oy + 7) / 8);
     if (a.prec == PREC_F32) k_remap<float2><<<grid, dim3(32, 8), 0, st>>>(a);
     else if (a.prec == PREC_F16) k_remap<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
