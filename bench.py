@@ -9,8 +9,8 @@ per-geometry FP64 tables (the paper's initialisation steps) are built once,
 before the timed region, and reported as init_ms.
 
 Default workload: 16384^2 complex64 point-cloud hologram, 532 nm, 0.307 um
-pitch (120 deg FoV), 20000 seeded points in z in [2, 10] mm, full 16384^2
-intensity view at z = 6 mm.  Inputs (2 GiB hologram, 8.6 GB spectrum) exceed
+pitch (120 deg FoV), 20000 seeded points in z in [0.6, 3.16] m, full 16384^2
+intensity view at z = 0.8 m.  Inputs (2 GiB hologram, 8.6 GB spectrum) exceed
 L2, so no L2 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -37,17 +37,18 @@ FALLBACK_HBM_GBS = 6800.0
 
 def _workload(name):
     from synth import configs
-    return {"uwa16k": configs.UWA_16K, "wa4096": configs.WA_4096, "small512": configs.SMALL_512}[name]
+    return {"uwa16k": configs.UWA_16K, "wa4096": configs.WA_4096, "small512": configs.SMALL_512,
+            "strip16k": configs.STRIP_16K}[name]
 
 
 def _config(w, extra=None):
-    c = {"workload": w.name, "hologram": "%dx%d complex64" % (w.n, w.n),
+    c = {"workload": w.name, "hologram": "%dx%d complex64" % (w.n, w.rows),
          "wavelength_nm": round(w.wavelength * 1e9, 3), "pitch_um": round(w.pitch * 1e6, 4),
-         "points": w.n_points, "z_points_mm": [w.z_range[0] * 1e3, w.z_range[1] * 1e3],
-         "view": "full %dx%d intensity at z = %g mm" % (w.n, w.n, w.z_view * 1e3),
+         "points": w.n_points, "z_points_m": [w.z_range[0], w.z_range[1]],
+         "view": "full %dx%d intensity at z = %g m" % (w.n, w.rows, w.z_view),
          "step": "FFT2 of a new hologram + stretch + FrT + remap (tables built once)",
          "l2_flush": "none: inputs larger than L2 (hologram %.1f GiB, spectrum %.1f GiB)"
-                     % (8 * w.n * w.n / 2 ** 30, 32 * w.n * w.n / 2 ** 30),
+                     % (8 * w.n * w.rows / 2 ** 30, 32 * w.n * w.rows / 2 ** 30),
          "parallelism": "replicas"}
     if extra:
         c.update(extra)
@@ -212,14 +213,14 @@ def run_ours(args, w):
     from paper_2410_13474_gb300 import build as b
     b.build()
     stream = torch.cuda.current_stream()
-    n = w.n
+    n, ny = w.n, w.rows
     pts = w.point_cloud()
     t0 = time.time()
-    d_holo = synth.gpu_hologram(pts, w.wavelength, w.pitch, n, n)
+    d_holo = synth.gpu_hologram(pts, w.wavelength, w.pitch, n, ny)
     gen_s = time.time() - t0
     torch.cuda.synchronize()
     t0 = time.time()
-    plan = nf.Plan(w.wavelength, w.pitch, n, n)
+    plan = nf.Plan(w.wavelength, w.pitch, n, ny)
     torch.cuda.synchronize()
     init_ms = (time.time() - t0) * 1e3
     view = nf.View(z=w.z_view)
@@ -255,7 +256,7 @@ def run_ours(args, w):
     stats = plan.profile_read()
 
     # end to end through the public API with host buffers
-    h_holo = torch.empty((n, n), dtype=torch.complex64, pin_memory=True)
+    h_holo = torch.empty((ny, n), dtype=torch.complex64, pin_memory=True)
     h_holo.copy_(d_holo)
     h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
     d_in = torch.empty_like(d_holo)
@@ -314,7 +315,7 @@ def run_ours(args, w):
     ref_out = out.clone()
     variants = {}
     for vname, prec in (("fp16_store", nf.FP16_STORE), ("bf16_store", nf.BF16_STORE)):
-        vp = nf.Plan(w.wavelength, w.pitch, n, n, precision=prec)
+        vp = nf.Plan(w.wavelength, w.pitch, n, ny, precision=prec)
         vout = vp.output_like(view)
         vp.load(d_holo)
         vp.reconstruct(view, vout)

@@ -32,6 +32,11 @@ class Workload:
     spread: float = 1.0          # points lie within spread * full-view half width
     partial_views: int = 0       # number of seeded partial views
     partial_size: int = 0        # their size in full-view pixels
+    ny: int = 0                  # rows of the hologram when not square (0: n)
+
+    @property
+    def rows(self) -> int:
+        return self.ny or self.n
 
     @property
     def tan_half(self) -> float:
@@ -42,7 +47,8 @@ class Workload:
                       self.spread)
 
     def make_hologram(self, threads: int = 0) -> np.ndarray:
-        return hologram(self.point_cloud(), self.wavelength, self.pitch, self.n, self.n, threads)
+        return hologram(self.point_cloud(), self.wavelength, self.pitch, self.n, self.rows,
+                        threads)
 
     def partial_view_offsets(self) -> np.ndarray:
         """Seeded view centres as integer full-view pixel offsets from the centre.
@@ -58,17 +64,26 @@ class Workload:
 
 # Full-view reconstruction of a small CGH (8 points, unit amplitude).
 SMALL_512 = Workload("pointcloud-512-532nm-0.4um-8pt", 512, LAMBDA_532, 0.4e-6, 8,
-                     (0.5e-3, 2.0e-3), (1.0, 1.0), 1.0e-3, seed=20241017)
-# Wide-angle 4096^2, 2000 points in a frustum z in [1, 5] mm, full view at 3 mm.
+                     (0.3, 0.7), (1.0, 1.0), 0.5, seed=20241017)
+# Wide-angle 4096^2 (64 deg), 2000 points in a frustum z in [0.5, 1.5] m, full
+# view at 0.85 m (the depths of the 8K wide-angle tests of Section 5).
 WA_4096 = Workload("pointcloud-4096-532nm-0.5um-2000pt", 4096, LAMBDA_532, 0.5e-6, 2000,
-                   (1.0e-3, 5.0e-3), (0.5, 1.0), 3.0e-3, seed=20241018)
-# Ultra-wide-angle 16384^2 (120 deg), 20000 points in z in [2, 10] mm,
-# full view at 6 mm plus 16 partial views of 2048^2 at the full-view pitch.
+                   (0.5, 1.5), (0.5, 1.0), 0.85, seed=20241018)
+# Ultra-wide-angle 16384^2 (120 deg), 20000 points in z in [0.6, 3.16] m (the
+# object of the 16K test of Section 5: front at 0.6 m, 2.56 m deep), full view
+# at 0.8 m (its Fig. 10a depth) plus 16 partial views of 2048^2 at the
+# full-view pitch.
 UWA_16K = Workload("pointcloud-16384-532nm-0.307um-20000pt", 16384, LAMBDA_532, 0.307e-6,
-                   20000, (2.0e-3, 10.0e-3), (0.5, 1.0), 6.0e-3, seed=20241019,
+                   20000, (0.6, 3.16), (0.5, 1.0), 0.8, seed=20241019,
                    partial_views=16, partial_size=2048)
 
-ALL = {w.name: w for w in (SMALL_512, WA_4096, UWA_16K)}
+# A 16384 x 2048 strip of the ultra-wide-angle geometry: its full view runs
+# the same 23040-point Fresnel rows along x as the 16K view, on 5760 rows
+# (about 3 GB of pass traffic), a size for detailed kernel captures.
+STRIP_16K = Workload("strip-16384x2048-532nm-0.307um-2000pt", 16384, LAMBDA_532, 0.307e-6,
+                     2000, (0.6, 3.16), (0.5, 1.0), 0.8, seed=20241023, ny=2048)
+
+ALL = {w.name: w for w in (SMALL_512, WA_4096, UWA_16K, STRIP_16K)}
 
 
 @dataclass(frozen=True)
@@ -82,20 +97,20 @@ class BatchRequest:
 
 def batch_workload(seed: int = 20241020, n_holo: int = 8, n_req: int = 64, lam: float = LAMBDA_532,
                    sizes=(2048, 4096, 8192), view_sizes=(256, 512, 1024, 2048, 4096),
-                   z_range=(1.0e-3, 8.0e-3), max_fft: int = 24576):
+                   z_range=(0.5, 3.0), max_fft: int = 24576):
     """Holograms of seeded sizes and pitches, and partial-view requests of
     uneven size, position and depth over them (the batched workload).  A
     request's z is drawn in [max(z_min, z_chirp), z_max], where z_chirp keeps
     the FFT size of the Fresnel stage within max_fft ((N pitch)^2/(lambda z)
-    <= max_fft)."""
+    <= max_fft); at the paper's object depths (0.5-3 m) it does not bind."""
     rng = np.random.default_rng(seed)
     holos = []
     for i in range(n_holo):
         n = int(rng.choice(sizes))
         pitch = float(rng.uniform(0.3e-6, 0.5e-6))
         npts = int(rng.integers(500, 5001))
-        holos.append(Workload("batch-holo-%d-%d" % (i, n), n, lam, pitch, npts, (1.0e-3, 8.0e-3),
-                              (0.5, 1.0), 4.0e-3, seed=seed * 100 + i))
+        holos.append(Workload("batch-holo-%d-%d" % (i, n), n, lam, pitch, npts, z_range,
+                              (0.5, 1.0), 1.0, seed=seed * 100 + i))
     reqs = []
     for _ in range(n_req):
         h = int(rng.integers(0, n_holo))
@@ -112,13 +127,13 @@ def batch_workload(seed: int = 20241020, n_holo: int = 8, n_req: int = 64, lam: 
 def serve_workload(seed: int = 20241021, n_holo: int = 12, n_req: int = 10000, rate: float = 200.0,
                    lam: float = LAMBDA_532, sizes=(2048, 4096, 8192, 16384),
                    view_sizes=(256, 512, 1024, 2048, 4096), max_fft: int = 24576,
-                   resident_cap_bytes: float = 72e9):
+                   resident_cap_bytes: float = 72e9, z_range=(0.6, 3.2)):
     """Resident holograms and a seeded Poisson stream of view requests (the
     serving workload).  Hologram sizes are drawn from `sizes` until the
     resident set (spectrum 32 N^2 B plus tables ~30 N^2 B each) would pass
     resident_cap_bytes; then the smallest size is used.  A request's z is drawn
-    in [max(2 mm, z_chirp), 10 mm] (z_chirp keeps the Fresnel-stage FFT within
-    max_fft).  Returns (holograms, requests, arrival_times)."""
+    in [max(z_min, z_chirp), z_max] (z_chirp keeps the Fresnel-stage FFT within
+    max_fft; at the paper's object depths of 0.5-3 m it does not bind).  Returns (holograms, requests, arrival_times)."""
     rng = np.random.default_rng(seed)
     holos, resident = [], 0.0
     for i in range(n_holo):
@@ -128,8 +143,8 @@ def serve_workload(seed: int = 20241021, n_holo: int = 12, n_req: int = 10000, r
         resident += 62.0 * n * n
         pitch = float(rng.uniform(0.307e-6, 0.5e-6))
         npts = int(rng.integers(500, 5001))
-        holos.append(Workload("serve-holo-%d-%d" % (i, n), n, lam, pitch, npts, (2.0e-3, 10.0e-3),
-                              (0.5, 1.0), 6.0e-3, seed=seed * 100 + i))
+        holos.append(Workload("serve-holo-%d-%d" % (i, n), n, lam, pitch, npts, z_range,
+                              (0.5, 1.0), 1.0, seed=seed * 100 + i))
     reqs = []
     for _ in range(n_req):
         h = int(rng.integers(0, n_holo))
@@ -138,7 +153,7 @@ def serve_workload(seed: int = 20241021, n_holo: int = 12, n_req: int = 10000, r
         lim = (w.n - s) // 2
         dx, dy = (int(v) for v in rng.integers(-lim, lim + 1, size=2))
         zc = (w.n * w.pitch) ** 2 / (lam * max_fft) * 1.02
-        z = float(rng.uniform(max(2.0e-3, zc), 10.0e-3))
+        z = float(rng.uniform(max(z_range[0], zc), z_range[1]))
         reqs.append(BatchRequest(h, s, dx, dy, z))
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     return holos, reqs, t
