@@ -76,7 +76,7 @@ struct nufds_plan {
     float2 *pb_frac = nullptr;
     // output map on the full-view pixel lattice (z independent)
     short2 *rm_base = nullptr;
-    float2 *rm_frac = nullptr;
+    uint2 *rm_frac = nullptr;
     // cached oversampled spectrum, [mx][my], in the plan's storage precision
     int prec = NUFDS_FP32;
     void *G = nullptr;
@@ -293,8 +293,8 @@ static int view_ws(const nufds_plan *P, const ViewPlan &V, const FftPlan *fpx, c
     w->ey_b0 = 2 * V.klo_y - 8;
     w->nbx = (int)(2 * (V.khi_x - V.klo_x) + 17);
     w->nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
-    w->outc = kind == NUFDS_OUT_FIELD_C64 ? align256(sizeof(float2) * (w->nbx + w->nby)) : 0;
-    w->rm = V.lattice ? 0 : align256((sizeof(short2) + sizeof(float2)) * (size_t)V.ox * V.oy + 256);
+    w->outc = kind == NUFDS_OUT_FIELD_C64 ? align256(sizeof(OutChirp) * (w->nbx + w->nby)) : 0;
+    w->rm = V.lattice ? 0 : align256((sizeof(short2) + sizeof(uint2)) * (size_t)V.ox * V.oy + 256);
     w->total = w->A + w->B + w->scr + w->chirp + w->outc + w->rm;
     (void)P;
     return NUFDS_OK;
@@ -398,17 +398,17 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     p += W.scr;
     float2 *chx = (float2 *)p, *chy = chx + V.npx;
     p += W.chirp;
-    float2 *Ex = (float2 *)p, *Ey = Ex + W.nbx;
+    OutChirp *Ex = (OutChirp *)p, *Ey = Ex + W.nbx;
     p += W.outc;
     short2 *rmb = P->rm_base;
-    float2 *rmf = P->rm_frac;
+    uint2 *rmf = P->rm_frac;
     long rm_ld = P->nx, rm_i0 = 0, rm_j0 = 0;
     if (V.lattice) {
         rm_i0 = V.i0;
         rm_j0 = V.j0;
     } else {
-        rmf = (float2 *)p;
-        rmb = (short2 *)(p + align256(sizeof(float2) * (size_t)V.ox * V.oy));
+        rmf = (uint2 *)p;
+        rmb = (short2 *)(p + align256(sizeof(uint2) * (size_t)V.ox * V.oy));
         rm_ld = V.ox;
         if ((rc = stage(P, ST_TABLES, 12.0 * V.ox * V.oy, st, [&] {
                  return launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px,
@@ -428,7 +428,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     const double kx = M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch));
     const double ky = M_PI * P->lam * V.z / ((P->ny * P->pitch) * (P->ny * P->pitch));
     if (v->out_kind == NUFDS_OUT_FIELD_C64) {
-        if ((rc = stage(P, ST_TABLES, 8.0 * (W.nbx + W.nby), st, [&] {
+        if ((rc = stage(P, ST_TABLES, 16.0 * (W.nbx + W.nby), st, [&] {
                  int r = launch_outchirp_table(kx, W.ex_b0, W.nbx, Ex, st);
                  return r ? r : launch_outchirp_table(ky, W.ey_b0, W.nby, Ey, st);
              })))
@@ -510,8 +510,8 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ra.Ey = Ey;
     ra.ex_b0 = W.ex_b0;
     ra.ey_b0 = W.ey_b0;
-    ra.kappa_x = (float)kx;
-    ra.kappa_y = (float)ky;
+    ra.k2x = turns_fx32(kx / (8.0 * M_PI));
+    ra.k2y = turns_fx32(ky / (8.0 * M_PI));
     ra.out = d_out;
     ra.prec = P->prec;
     ra.sc_q = scale_ptr(P, 5);
@@ -590,8 +590,8 @@ static size_t view_batch_bytes(const BatchView &b, int prec) {
     size_t t = align256(eb * 4 * np) + align256(eb * 2 * np) +
                align256(sizeof(float2) * (b.V.npx + b.V.npy)) + 256;
     if (b.kind == NUFDS_OUT_FIELD_C64)
-        t += align256(sizeof(float2) * (4 * (b.V.khi_x - b.V.klo_x) + 4 * (b.V.khi_y - b.V.klo_y) + 68));
-    if (!b.V.lattice) t += 2 * align256((sizeof(short2) + sizeof(float2)) * (size_t)b.V.ox * b.V.oy);
+        t += align256(sizeof(OutChirp) * (4 * (b.V.khi_x - b.V.klo_x) + 4 * (b.V.khi_y - b.V.klo_y) + 68));
+    if (!b.V.lattice) t += 2 * align256((sizeof(short2) + sizeof(uint2)) * (size_t)b.V.ox * b.V.oy);
     return t;
 }
 
@@ -691,9 +691,10 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
     const size_t eb = prec_bytes(prec);
     struct Regions {
         void *A, *Bf;
-        float2 *chx, *chy, *Ex, *Ey;
+        float2 *chx, *chy;
+        OutChirp *Ex, *Ey;
         short2 *rmb;
-        float2 *rmf;
+        uint2 *rmf;
         float *sc;
         double *acc;
         long ex_b0, ey_b0;
@@ -724,9 +725,9 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         g.nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
         g.Ex = g.Ey = nullptr;
         if (b.kind == NUFDS_OUT_FIELD_C64) {
-            g.Ex = (float2 *)p;
+            g.Ex = (OutChirp *)p;
             g.Ey = g.Ex + g.nbx;
-            p += align256(sizeof(float2) * (4 * (V.khi_x - V.klo_x) + 4 * (V.khi_y - V.klo_y) + 68));
+            p += align256(sizeof(OutChirp) * (g.nbx + g.nby));
         }
         g.rmb = P->rm_base;
         g.rmf = P->rm_frac;
@@ -735,8 +736,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
             rm_i0 = V.i0;
             rm_j0 = V.j0;
         } else {
-            g.rmf = (float2 *)p;
-            g.rmb = (short2 *)(p + align256(sizeof(float2) * (size_t)V.ox * V.oy));
+            g.rmf = (uint2 *)p;
+            g.rmb = (short2 *)(p + align256(sizeof(uint2) * (size_t)V.ox * V.oy));
             rm_ld = V.ox;
         }
         const float *scG = prec == NUFDS_FP16_STORE ? P->sc + 1 : nullptr;
@@ -818,8 +819,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         ra.Ey = g.Ey;
         ra.ex_b0 = g.ex_b0;
         ra.ey_b0 = g.ey_b0;
-        ra.kappa_x = (float)(M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch)));
-        ra.kappa_y = (float)(M_PI * P->lam * V.z / ((P->ny * P->pitch) * (P->ny * P->pitch)));
+        ra.k2x = turns_fx32(P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch)) / 8.0);
+        ra.k2y = turns_fx32(P->lam * V.z / ((P->ny * P->pitch) * (P->ny * P->pitch)) / 8.0);
         ra.out = b.out;
         ra.prec = prec;
         ra.sc_q = scQ;
@@ -1058,7 +1059,7 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     if (cudaMalloc(&P->pb_base, npb * sizeof(short2)) != cudaSuccess ||
         cudaMalloc(&P->pb_frac, npb * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&P->rm_base, npix * sizeof(short2)) != cudaSuccess ||
-        cudaMalloc(&P->rm_frac, npix * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&P->rm_frac, npix * sizeof(uint2)) != cudaSuccess ||
         cudaMalloc(&P->G, 4 * npix * prec_bytes(P->prec)) != cudaSuccess ||
         cudaMalloc(&P->sc, 256) != cudaSuccess) {
         cudaGetLastError();
@@ -1278,7 +1279,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     short2 *pbb = c.take<short2>((size_t)pb_nkx * pb_nky);
     float2 *pbf = c.take<float2>((size_t)pb_nkx * pb_nky);
     short2 *rmb = c.take<short2>(npix);
-    float2 *rmf = c.take<float2>(npix);
+    uint2 *rmf = c.take<uint2>(npix);
     float2 *A = c.take<float2>(4 * (np2 > npix ? np2 : npix));
     float2 *Bf = c.take<float2>(2 * (np2 > npix ? np2 : npix));
     float2 *chx = c.take<float2>(V.npx), *chy = c.take<float2>(V.npy);
@@ -1292,21 +1293,21 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     float2 *scr = c.take<float2>(sy > sx ? sy : sx);
     const long ex_b0 = 2 * V.klo_x - 8, ey_b0 = 2 * V.klo_y - 8;
     const int nbx = (int)(2 * (V.khi_x - V.klo_x) + 17), nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
-    float2 *Ex = nullptr, *Ey = nullptr;
+    OutChirp *Ex = nullptr, *Ey = nullptr;
     if (v->out_kind == NUFDS_OUT_FIELD_C64) {
-        Ex = c.take<float2>(nbx);
-        Ey = c.take<float2>(nby);
+        Ex = c.take<OutChirp>(nbx);
+        Ey = c.take<OutChirp>(nby);
         if (!Ex || !Ey) return NUFDS_EUNSUPPORTED;
     }
     short2 *vrb = rmb;
-    float2 *vrf = rmf;
+    uint2 *vrf = rmf;
     long rm_ld = nx, rm_i0 = 0, rm_j0 = 0;
     if (V.lattice) {
         rm_i0 = V.i0;
         rm_j0 = V.j0;
     } else {
         vrb = c.take<short2>((size_t)V.ox * V.oy);
-        vrf = c.take<float2>((size_t)V.ox * V.oy);
+        vrf = c.take<uint2>((size_t)V.ox * V.oy);
         rm_ld = V.ox;
     }
     if (!scr || !vrb || !vrf) return NUFDS_EUNSUPPORTED;
@@ -1389,8 +1390,8 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     ra.Ey = Ey;
     ra.ex_b0 = ex_b0;
     ra.ey_b0 = ey_b0;
-    ra.kappa_x = (float)kx;
-    ra.kappa_y = (float)ky;
+    ra.k2x = turns_fx32(kx / (8.0 * M_PI));
+    ra.k2y = turns_fx32(ky / (8.0 * M_PI));
     ra.out = d_out;
     ra.prec = PREC_F32;
     ra.sc_q = nullptr;

@@ -190,12 +190,14 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const int j = by * 8 + threadIdx.y;
     const bool valid = i < a.ox && j < a.oy;
     short2 b = make_short2(0, 0);
-    float2 f = make_float2(0.f, 0.f);
+    uint2 F = make_uint2(0u, 0u);
     if (valid) {
         const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
         b = a.rm_base[t];
-        f = a.rm_frac[t];
+        F = a.rm_frac[t];
     }
+    // the fraction in FP32 for the weights (rounded toward zero: stays < 1)
+    const float2 f = make_float2(__uint2float_rz(F.x) * 0x1p-32f, __uint2float_rz(F.y) * 0x1p-32f);
     const int Mx = 2 * a.npx, My = 2 * a.npy;
     // first taps on the fine grid, unwrapped (rows = y, columns = x)
     const int c0 = (int)(b.x - 2 * a.kc_x) + a.npx - kW / 2 + 1;
@@ -228,13 +230,19 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     if (a.kind == 0) {
         ((float *)a.out)[o] = fmaf(acc.x, acc.x, acc.y * acc.y);
     } else {
-        // e^{i kappa t'^2} per axis, t' = (b + f) / 2: table for the b^2 part,
-        // FP32 for kappa (b f / 2 + f^2 / 4) (|.| < ~10 rad)
-        float2 ex = __ldg(a.Ex + (b.x - a.ex_b0)), ey = __ldg(a.Ey + (b.y - a.ey_b0));
-        float ph = a.kappa_x * (0.5f * (float)b.x * f.x + 0.25f * f.x * f.x) +
-                   a.kappa_y * (0.5f * (float)b.y * f.y + 0.25f * f.y * f.y);
+        // e^{i kappa (b + f)^2 / 4} per axis: the b^2 part from the table, the
+        // rest, kappa b f / 2 + kappa f^2 / 4, in turns reduced mod 1 exactly:
+        // bits 32..63 of K * F (K = kappa b / (4 pi) in 32.32, F = f 2^32) and
+        // of K2 * G (K2 = kappa / (8 pi), G = f^2 2^32).
+        const OutChirp cx = a.Ex[b.x - a.ex_b0], cy = a.Ey[b.y - a.ey_b0];
+        const unsigned int gx = __umulhi(F.x, F.x), gy = __umulhi(F.y, F.y);
+        unsigned int tq = __umulhi(cx.klo, F.x) + (unsigned int)cx.khi * F.x;
+        tq += __umulhi(cy.klo, F.y) + (unsigned int)cy.khi * F.y;
+        tq += __umulhi(a.k2x.x, gx) + a.k2x.y * gx;
+        tq += __umulhi(a.k2y.x, gy) + a.k2y.y * gy;
         float s, c;
-        sincosf(ph, &s, &c);
+        sincospif((float)(int)tq * 0x1p-31f, &s, &c);  // 2 pi (tq / 2^32), in (-pi, pi]
+        const float2 ex = cx.e, ey = cy.e;
         float2 e = make_float2(ex.x * ey.x - ex.y * ey.y, ex.x * ey.y + ex.y * ey.x);
         float2 w = make_float2(e.x * c - e.y * s, e.x * s + e.y * c);
         ((float2 *)a.out)[o] = make_float2(acc.x * w.x - acc.y * w.y, acc.x * w.y + acc.y * w.x);

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <vector>
@@ -174,16 +175,35 @@ double g_at_one();
 int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
                           int nky, short2 *base, float2 *frac, cudaStream_t st);
 // Output-map table for pixels x_o = cx + (i - ox/2) px etc. at distance z,
-// layout [j][i]; t' in stretched-lattice units, stored as floor(2t') + frac.
+// layout [j][i]; t' in stretched-lattice units, stored as b = floor(2t') and
+// the fraction 2t' - b in 0.32 fixed point (exact to 2^-32 of a fine cell:
+// the output chirp changes by up to thousands of radians per fine cell at
+// the paper's depths, so an FP32 fraction would cost 1e-4 rad).
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
-                       double px, double py, int ox, int oy, short2 *base, float2 *frac,
+                       double px, double py, int ox, int oy, short2 *base, uint2 *frac,
                        cudaStream_t st);
 // chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L at n = natural index of the
 // slot (digit-reversed order of plan fp), x_n = (n - L/2) window / L
 int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,
                        cudaStream_t st);
-// Output chirp pieces: E[b - b0] = e^{i kappa b^2 / 4} for b in [b0, b0 + nb)
-int launch_outchirp_table(double kappa, long b0, int nb, float2 *E, cudaStream_t st);
+// Output chirp e^{i kappa (b + f)^2 / 4} per axis (b fine base, f its
+// fraction), split so that every large argument is reduced exactly:
+//   e  = e^{i kappa b^2 / 4}          (FP64 phase, reduced, stored FP32),
+//   K  = kappa b / (4 pi)             (turns per unit of f, 32.32 fixed point,
+//                                      so K f mod 1 is exact integer arithmetic),
+// and the f^2 term kappa / (8 pi) f^2 turns from one per-axis constant.
+struct __align__(16) OutChirp {
+    float2 e;
+    unsigned int klo;  // low word of round(K 2^32)
+    int khi;           // high word (two's complement)
+};
+// E[b - b0] for b in [b0, b0 + nb); fails (-3) if |K| would pass 2^30 turns
+int launch_outchirp_table(double kappa, long b0, int nb, OutChirp *E, cudaStream_t st);
+// x 2^32 in two's complement, as (low word, high word); |turns| < 2^30
+inline uint2 turns_fx32(double turns) {
+    const long long v = llrint(turns * 4294967296.0);
+    return make_uint2((unsigned int)(v & 0xffffffffLL), (unsigned int)(v >> 32));
+}
 
 // ---------------------------------------------------------------------------
 // Gathers (gather.cu)
@@ -213,13 +233,13 @@ struct RemapArgs {
     int npx, npy;
     long kc_x, kc_y;
     const short2 *rm_base;  // output-map table, layout [j][i], row length rm_ld
-    const float2 *rm_frac;
+    const uint2 *rm_frac;   // its fractions, 0.32 fixed point
     long rm_ld, rm_i0, rm_j0;
     int ox, oy;
     int kind;               // 0 intensity f32, 1 field c64
-    const float2 *Ex, *Ey;  // output chirp tables (field only)
+    const OutChirp *Ex, *Ey;  // output chirp tables (field only)
     long ex_b0, ey_b0;
-    float kappa_x, kappa_y;
+    uint2 k2x, k2y;           // kappa / (8 pi) turns, 32.32 fixed point (low, high)
     void *out;
     int prec;               // storage of Q
     const float *sc_q;

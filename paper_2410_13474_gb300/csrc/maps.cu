@@ -14,6 +14,9 @@
 // 2x oversampled grid plus an FP32 fraction in [0, 1), which keeps ~1e-7 of
 // a fine cell after the FP32 kernels take over.
 #include <math.h>
+#include <stdlib.h>
+
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -161,11 +164,19 @@ __global__ void k_pullback_table(double lam, double pitch, int nx, int ny, long 
     frac[idx] = f;
 }
 
+// floor and 0.32 fixed-point fraction (truncated, so the fraction is < 1)
+__device__ inline void split_fine_fx(double t2, short *base, unsigned int *frac) {
+    double b = floor(t2);
+    *base = (short)b;
+    double q = floor((t2 - b) * 4294967296.0);
+    *frac = q >= 4294967295.0 ? 0xffffffffu : (unsigned int)q;
+}
+
 // Output map of Eq. 17 in stretched-lattice units t' = N pitch f_0 m(f_0),
 // f_0 = (x_o, y_o) / (lambda R_0), for view pixels; layout [j][i].
 __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z, double cx,
                               double cy, double px, double py, int ox, int oy, double g1,
-                              short2 *base, float2 *frac) {
+                              short2 *base, uint2 *frac) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)ox * oy) return;
     int j = (int)(idx / ox), i = (int)(idx - (long)j * ox);
@@ -175,9 +186,9 @@ __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z
     phi_uv(xo / R0, yo / R0, g1, &up, &vp);
     double tx = nx * pitch * up / lam, ty = ny * pitch * vp / lam;
     short2 b;
-    float2 f;
-    split_fine(2.0 * tx, &b.x, &f.x);
-    split_fine(2.0 * ty, &b.y, &f.y);
+    uint2 f;
+    split_fine_fx(2.0 * tx, &b.x, &f.x);
+    split_fine_fx(2.0 * ty, &b.y, &f.y);
     base[idx] = b;
     frac[idx] = f;
 }
@@ -199,7 +210,7 @@ __global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, f
     chirp[slot] = make_float2((float)(c * a), (float)(s * a));
 }
 
-__global__ void k_outchirp_table(double kappa, long b0, int nb, float2 *E) {
+__global__ void k_outchirp_table(double kappa, long b0, int nb, OutChirp *E) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     double b = (double)(b0 + i);
@@ -207,7 +218,12 @@ __global__ void k_outchirp_table(double kappa, long b0, int nb, float2 *E) {
     ph -= 2.0 * M_PI * rint(ph / (2.0 * M_PI));
     double s, c;
     sincos(ph, &s, &c);
-    E[i] = make_float2((float)c, (float)s);
+    OutChirp o;
+    o.e = make_float2((float)c, (float)s);
+    const long long k = llrint(kappa * b / (4.0 * M_PI) * 4294967296.0);
+    o.klo = (unsigned int)(k & 0xffffffffLL);
+    o.khi = (int)(k >> 32);
+    E[i] = o;
 }
 
 int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
@@ -221,7 +237,7 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
 }
 
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
-                       double px, double py, int ox, int oy, short2 *base, float2 *frac,
+                       double px, double py, int ox, int oy, short2 *base, uint2 *frac,
                        cudaStream_t st) {
     long n = (long)ox * oy;
     if (n <= 0) return 0;
@@ -238,7 +254,9 @@ int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z,
     return check_launch();
 }
 
-int launch_outchirp_table(double kappa, long b0, int nb, float2 *E, cudaStream_t st) {
+int launch_outchirp_table(double kappa, long b0, int nb, OutChirp *E, cudaStream_t st) {
+    const double bmax = (double)std::max(std::labs(b0), std::labs(b0 + nb));
+    if (!(fabs(kappa) * bmax / (4.0 * M_PI) < 1073741824.0)) return -3;
     k_outchirp_table<<<(nb + 255) / 256, 256, 0, st>>>(kappa, b0, nb, E);
     count_launch();
     return check_launch();
