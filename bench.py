@@ -505,7 +505,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uwa16k",
-                    choices=["uwa16k", "wa4096", "small512", "batch64", "serve"])
+                    choices=["uwa16k", "wa4096", "small512", "strip16k", "batch64", "serve"])
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
