@@ -223,11 +223,12 @@ __device__ __forceinline__ void dif_first_r(const PassArgs &P, const TI *__restr
     }
 }
 
-// last pass (P-1, stride 1) of the inverse DIF fused with the chirp (slot
-// order), a copy of the result to scratch, and the first forward DIT pass
+// last pass (P-1, stride 1) of the inverse DIF fused with the chirp, a copy
+// of the result to scratch, and the first forward DIT pass; chirp and
+// scratch in group-major order (slot g R + k at k ng + g: coalesced)
 template <int R>
 __device__ __forceinline__ void fused_mid_r(const PassArgs &P, float2 *sm,
-                                            const float2 *__restrict__ chirp_slot,
+                                            const float2 *__restrict__ chirp_gm,
                                             float2 *__restrict__ scr) {
     const int ng = P.L / R;
     for (int g = threadIdx.x; g < ng; g += blockDim.x) {
@@ -238,8 +239,8 @@ __device__ __forceinline__ void fused_mid_r(const PassArgs &P, float2 *sm,
         Dft<R, true>::run(x);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            x[k] = cmul(x[k], __ldg(chirp_slot + base + k));
-            scr[base + k] = x[k];
+            x[k] = cmul(x[k], __ldg(chirp_gm + k * ng + g));
+            scr[k * ng + g] = x[k];
         }
         Dft<R, false>::run(x);
 #pragma unroll
@@ -256,7 +257,7 @@ __device__ __forceinline__ void odd_first_r(const PassArgs &P, float2 *sm,
         const int base = g * R;
         float2 x[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) x[i] = cmul(scr[base + i], __ldg(P.mod1_slot + base + i));
+        for (int i = 0; i < R; ++i) x[i] = cmul(scr[i * ng + g], __ldg(P.mod1_slot + i * ng + g));
         Dft<R, false>::run(x);
 #pragma unroll
         for (int k = 0; k < R; ++k) sm[phys(base + k)] = x[k];
@@ -687,7 +688,7 @@ static int plan_host(int L, FftPlan &p, std::vector<float2> &f2, std::vector<dou
         double a = -M_PI * (n - L / 2) / (double)L;
         mod1[n] = make_float2((float)cos(a), (float)sin(a));
     }
-    for (int q = 0; q < L; ++q) mod1s[q] = mod1[slot_to_index(p, q)];
+    for (int q = 0; q < L; ++q) mod1s[fft_gm_pos(p, q)] = mod1[slot_to_index(p, q)];
     std::vector<double> ft;
     es_fourier(L, ft);
     dea.resize(L);

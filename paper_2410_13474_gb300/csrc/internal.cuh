@@ -84,7 +84,7 @@ struct FftPlan {
     // device tables (owned by the length cache, or caller memory)
     const float2 *tw = nullptr;        // W_L^j (j < 64) | W_L^{64 i} (i < ncoarse)
     const float2 *mod1 = nullptr;      // e^{-i pi (n - L/2)/L}, natural order
-    const float2 *mod1_slot = nullptr; // the same in digit-reversed slot order
+    const float2 *mod1_slot = nullptr; // the same per slot, group-major order (fft_gm_pos)
     const double *deapod = nullptr;    // 1 / psi_hat(n - L/2)
     const float *pad_pre = nullptr;    // (-1)^n / psi_hat(n - L/2)
 };
@@ -95,7 +95,7 @@ struct PassArgs {
     uint32_t mag_stride[kMaxPasses];  // ceil(2^32 / stride), 0 for stride 1
     uint32_t mag_radix[kMaxPasses];   // ceil(2^32 / radix)
     const float2 *tw;                 // fine[64] | coarse[ncoarse]: W_L^q = coarse[q>>6] fine[q&63]
-    const float2 *mod1, *mod1_slot;   // e^{-i pi (n - L/2)/L}: natural / slot order
+    const float2 *mod1, *mod1_slot;   // e^{-i pi (n - L/2)/L}: natural / per slot, group-major
     const float *pad_pre;             // (-1)^n / psi_hat(n - L/2), natural order
 };
 
@@ -130,6 +130,15 @@ __host__ __device__ inline int fft_index_of_slot(const FftPlan &p, int slot) {
     int n = 0;
     for (int j = 0; j < p.npass; ++j) n += ((slot / p.stride[j]) % p.radix[j]) * p.prefix[j];
     return n;
+}
+// Position of digit-reversed slot q in the group-major order of the last
+// pass (radix R, L / R groups): element k of group g (slot g R + k) at
+// k (L / R) + g, so that lanes handling consecutive groups touch
+// consecutive addresses.  The per-slot tables (chirp, odd-half modulation)
+// and the odd-half scratch are kept in this order.
+__host__ __device__ inline int fft_gm_pos(const FftPlan &p, int q) {
+    const int R = p.radix[p.npass - 1];
+    return (q % R) * (p.L / R) + q / R;
 }
 // float2 count of the twiddle/modulation table of length L
 size_t fft_tw_count(int L);

@@ -193,7 +193,8 @@ __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z
     frac[idx] = f;
 }
 
-// chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) window / L,
+// chirp at the group-major position of each slot:
+// e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) window / L,
 // n the natural index of the slot in the digit-reversed order of the row FFT
 __global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, float2 *chirp) {
     const int L = fp.L;
@@ -207,7 +208,7 @@ __global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, f
     double s, c;
     sincos(ph, &s, &c);
     double a = deapod[n] / L;
-    chirp[slot] = make_float2((float)(c * a), (float)(s * a));
+    chirp[fft_gm_pos(fp, slot)] = make_float2((float)(c * a), (float)(s * a));
 }
 
 __global__ void k_outchirp_table(double kappa, long b0, int nb, OutChirp *E) {
