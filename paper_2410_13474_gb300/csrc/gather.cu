@@ -27,20 +27,29 @@ namespace nufds {
 // Kernel weights of the kW taps for a fractional offset f in [0, 1): tap i is
 // at distance d_i = f + kW/2 - 1 - i and weighs psi(d_i) =
 // exp(beta (sqrt(1 - (2 d_i / kW)^2) - 1)).  Each psi(f + c_i) is smooth in f,
-// so it is evaluated as a degree-kEsDeg polynomial in t = 2f - 1 whose
+// so it is evaluated as a degree-kEsDeg polynomial P_i in t = 2f - 1 whose
 // coefficients are Chebyshev interpolants built in FP64 on the host (max
-// error ~1e-7 absolute, weights <= 1).
+// error ~1e-7 absolute, weights <= 1).  psi is even, so tap kW-1-i at f is
+// tap i at 1 - f: P_{kW-1-i}(t) = P_i(-t).  With P_i(t) = E_i(t^2) + t O_i(t^2)
+// both taps come from one evaluation of E_i and O_i.
 constexpr int kEsDeg = 12;
-__constant__ float c_es[kW][kEsDeg + 1];
+constexpr int kEsEven = kEsDeg / 2 + 1;  // coefficients of E_i (t^0, t^2, ..)
+constexpr int kEsOdd = kEsDeg / 2;       // coefficients of O_i (t^1, t^3, ..)
+__constant__ float c_es_e[kW / 2][kEsEven];
+__constant__ float c_es_o[kW / 2][kEsOdd];
 
 __device__ __forceinline__ void es_weights(float f, float *w) {
-    const float t = 2.0f * f - 1.0f;
+    const float t = 2.0f * f - 1.0f, u = t * t;
 #pragma unroll
-    for (int i = 0; i < kW; ++i) {
-        float p = c_es[i][kEsDeg];
+    for (int i = 0; i < kW / 2; ++i) {
+        float e = c_es_e[i][kEsEven - 1];
 #pragma unroll
-        for (int k = kEsDeg - 1; k >= 0; --k) p = fmaf(p, t, c_es[i][k]);
-        w[i] = p;
+        for (int k = kEsEven - 2; k >= 0; --k) e = fmaf(e, u, c_es_e[i][k]);
+        float o = c_es_o[i][kEsOdd - 1];
+#pragma unroll
+        for (int k = kEsOdd - 2; k >= 0; --k) o = fmaf(o, u, c_es_o[i][k]);
+        w[i] = fmaf(t, o, e);
+        w[kW - 1 - i] = fmaf(-t, o, e);
     }
 }
 
@@ -49,8 +58,9 @@ static double psi_host(double d) {
     return q > 0.0 ? exp(kBeta * (sqrt(q) - 1.0)) : 0.0;
 }
 
-// Chebyshev interpolation of each tap's weight on kEsDeg + 1 nodes, converted
-// to monomial coefficients in t; uploaded once per device.
+// Chebyshev interpolation of the weight of taps 0 .. kW/2-1 on kEsDeg + 1
+// nodes, converted to monomial coefficients in t and split into even and odd
+// parts; uploaded once per device.
 static int es_init() {
     static std::mutex mu;
     static std::map<int, bool> ready;
@@ -59,8 +69,8 @@ static int es_init() {
     std::lock_guard<std::mutex> lk(mu);
     if (ready[dev]) return 0;
     const int n = kEsDeg + 1;
-    float h[kW][kEsDeg + 1];
-    for (int i = 0; i < kW; ++i) {
+    float he[kW / 2][kEsEven], ho[kW / 2][kEsOdd];
+    for (int i = 0; i < kW / 2; ++i) {
         double a[kEsDeg + 1] = {0};
         for (int k = 0; k < n; ++k) {
             double s = 0;
@@ -89,9 +99,12 @@ static int es_init() {
                 mono[m] += a[k] * nx[m];
             }
         }
-        for (int m = 0; m <= kEsDeg; ++m) h[i][m] = (float)mono[m];
+        for (int m = 0; m < kEsEven; ++m) he[i][m] = (float)mono[2 * m];
+        for (int m = 0; m < kEsOdd; ++m) ho[i][m] = (float)mono[2 * m + 1];
     }
-    if (cudaMemcpyToSymbol(c_es, h, sizeof(h)) != cudaSuccess) return -4;
+    if (cudaMemcpyToSymbol(c_es_e, he, sizeof(he)) != cudaSuccess ||
+        cudaMemcpyToSymbol(c_es_o, ho, sizeof(ho)) != cudaSuccess)
+        return -4;
     ready[dev] = true;
     return 0;
 }
@@ -99,6 +112,40 @@ static int es_init() {
 // m in [-M, 2M): periodic index without integer division
 __device__ __forceinline__ int wrap(int m, int M) {
     return m < 0 ? m + M : (m >= M ? m - M : m);
+}
+
+// sum_{i,j} wr[i] wc[j] A[row r0 + i][column c0 + j] for a window inside a
+// grid stored plane-wise on both axes (fine row m at row (m & 1) Lr + (m >> 1),
+// pitch ld; fine column m at (m & 1) Lc + (m >> 1)): 0 <= r0, r0 + kW <= 2 Lr,
+// 0 <= c0, c0 + kW <= 2 Lc.  The kW columns of a row are two runs of kW/2
+// consecutive elements (even taps in one plane, odd taps in the other), so
+// each run is one pointer and its loads take immediate offsets.  Same
+// summation order as the general path.
+template <class T>
+__device__ __forceinline__ float2 window_sum_inside(const T *__restrict__ A, long ld, int Lr,
+                                                   int Lc, int r0, int c0, const float *wr,
+                                                   const float *wc) {
+    const int e = c0 & 1;
+    const int ca = e * Lc + (c0 >> 1), cb = (1 - e) * Lc + ((c0 + 1) >> 1);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kW; ++i) {
+        const int r = r0 + i;
+        const T *row = A + (long)((r & 1) * Lr + (r >> 1)) * ld;
+        const T *pa = row + ca, *pb = row + cb;
+        float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < kW / 2; ++q) {
+            const float2 ga = ld_c(pa, q, 1.0f), gb = ld_c(pb, q, 1.0f);
+            sum.x = fmaf(wc[2 * q], ga.x, sum.x);
+            sum.y = fmaf(wc[2 * q], ga.y, sum.y);
+            sum.x = fmaf(wc[2 * q + 1], gb.x, sum.x);
+            sum.y = fmaf(wc[2 * q + 1], gb.y, sum.y);
+        }
+        acc.x = fmaf(wr[i], sum.x, acc.x);
+        acc.y = fmaf(wr[i], sum.y, acc.y);
+    }
+    return acc;
 }
 
 template <class T>
@@ -128,7 +175,9 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
         float wx[kW], wy[kW];
         es_weights(f.x, wx);
         es_weights(f.y, wy);
-        {
+        if (r0 >= 0 && r0 + kW <= Mx && c0 >= 0 && c0 + kW <= My) {
+            acc = window_sum_inside(G, My, a.Nx, a.Ny, r0, c0, wx, wy);
+        } else {  // the window wraps around the periodic grid
             int cols[kW];
 #pragma unroll
             for (int j = 0; j < kW; ++j) cols[j] = fine_pos(wrap(c0 + j, My), a.Ny);
@@ -207,7 +256,9 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     float wx[kW], wy[kW];
     es_weights(f.x, wx);
     es_weights(f.y, wy);
-    {
+    if (r0 >= 0 && r0 + kW <= My && c0 >= 0 && c0 + kW <= Mx) {
+        acc = window_sum_inside(Q, Mx, a.npy, a.npx, r0, c0, wy, wx);
+    } else {  // the window wraps around the periodic grid
         int cols[kW];
 #pragma unroll
         for (int q = 0; q < kW; ++q) cols[q] = fine_pos(wrap(c0 + q, Mx), a.npx);
