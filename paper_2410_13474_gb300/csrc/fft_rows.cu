@@ -724,11 +724,19 @@ static int grid_for(const void *fn, const FftPlan &p, int rows);
 
 // Autotuner of the row passes: time the view pass (the heaviest) with each
 // candidate block size on zeroed buffers and keep the fastest (per device and
-// length, once).  Falls back to the default on any failure.
+// length, once).  The probe gives every resident CTA four rows, so it measures
+// the steady state rather than a one-row tail.  Falls back to the default on
+// any failure.
 static void autotune_threads(FftPlan &p) {
     const int L = p.L;
-    const int rows = std::min(256, 2 * L);
-    int cands[3] = {128, 256, 512}, best_t = p.threads;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_rows_view<float2>, 128,
+                                                  p.smem_bytes);
+    const long cap = (512L << 20) / (24L * L);  // in + 2x out + scratch under ~512 MB
+    const int rows = (int)std::max(1L, std::min(4L * std::max(sms, 1) * std::max(per, 1), cap));
+    int cands[5] = {128, 192, 256, 384, 512}, best_t = p.threads;
     float best = 1e30f;
     float2 *in = nullptr, *out = nullptr, *scr = nullptr, *chirp = nullptr;
     cudaStream_t st = nullptr;
