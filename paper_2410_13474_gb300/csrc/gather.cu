@@ -16,6 +16,7 @@
 // (m & 1) * L + m / 2), as the row passes write them.
 #include <math.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <map>
 #include <mutex>
@@ -121,7 +122,52 @@ __device__ __forceinline__ int wrap(int m, int M) {
 // consecutive elements (even taps in one plane, odd taps in the other), so
 // each run is one pointer and its loads take immediate offsets.  Same
 // summation order as the general path.
-template <class T>
+// Four consecutive elements row[s .. s+3] as two 2-element vector loads from
+// the aligned-down start, plus one single load of the last element when s is
+// odd (rows start on 2-element boundaries: A is 256-byte aligned and every
+// pitch is even).  Fewer, wider requests than four single loads: fewer L1
+// tag lookups, more data-pipe wavefronts per request -- a gain where lanes
+// are far apart (the remap), a loss where their windows overlap (the stretch).
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ void load_run4(const float2 *__restrict__ row, int s, float2 *v) {
+    const bool odd = s & 1;
+    const float4 *q = reinterpret_cast<const float4 *>(row + (s & ~1));
+    const float4 f0 = __ldg(q), f1 = __ldg(q + 1);
+    float2 f2 = make_float2(0.f, 0.f);
+    if (odd) f2 = __ldg(row + s + 3);
+    v[0] = odd ? hi2(f0) : lo2(f0);
+    v[1] = odd ? lo2(f1) : hi2(f0);
+    v[2] = odd ? hi2(f1) : lo2(f1);
+    v[3] = odd ? f2 : hi2(f1);
+}
+__device__ __forceinline__ float2 cvt_c(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 cvt_c(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <class H>
+__device__ __forceinline__ void load_run4_16(const H *__restrict__ row, int s, float2 *v) {
+    const bool odd = s & 1;
+    const uint2 *q = reinterpret_cast<const uint2 *>(row + (s & ~1));
+    const uint2 f0 = __ldg(q), f1 = __ldg(q + 1);
+    unsigned int f2 = 0u;
+    if (odd) f2 = __ldg(reinterpret_cast<const unsigned int *>(row + s + 3));
+    const unsigned int w[5] = {f0.x, f0.y, f1.x, f1.y, f2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned int u = odd ? w[k + 1] : w[k];
+        H h;
+        memcpy(&h, &u, sizeof(h));
+        v[k] = cvt_c(h);
+    }
+}
+__device__ __forceinline__ void load_run4(const __half2 *__restrict__ row, int s, float2 *v) {
+    load_run4_16(row, s, v);
+}
+__device__ __forceinline__ void load_run4(const __nv_bfloat162 *__restrict__ row, int s,
+                                          float2 *v) {
+    load_run4_16(row, s, v);
+}
+
+template <bool WIDE, class T>
 __device__ __forceinline__ float2 window_sum_inside(const T *__restrict__ A, long ld, int Lr,
                                                    int Lc, int r0, int c0, const float *wr,
                                                    const float *wc) {
@@ -132,11 +178,21 @@ __device__ __forceinline__ float2 window_sum_inside(const T *__restrict__ A, lon
     for (int i = 0; i < kW; ++i) {
         const int r = r0 + i;
         const T *row = A + (long)((r & 1) * Lr + (r >> 1)) * ld;
-        const T *pa = row + ca, *pb = row + cb;
+        float2 va[kW / 2], vb[kW / 2];
+        if (WIDE) {
+            load_run4(row, ca, va);
+            load_run4(row, cb, vb);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kW / 2; ++q) {
+                va[q] = ld_c(row + ca, q, 1.0f);
+                vb[q] = ld_c(row + cb, q, 1.0f);
+            }
+        }
         float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < kW / 2; ++q) {
-            const float2 ga = ld_c(pa, q, 1.0f), gb = ld_c(pb, q, 1.0f);
+            const float2 ga = va[q], gb = vb[q];
             sum.x = fmaf(wc[2 * q], ga.x, sum.x);
             sum.y = fmaf(wc[2 * q], ga.y, sum.y);
             sum.x = fmaf(wc[2 * q + 1], gb.x, sum.x);
@@ -152,6 +208,8 @@ template <class T>
 __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int by) {
     const T *G = (const T *)a.G;
     const float ginv = a.sc_g ? 1.0f / *a.sc_g : 1.0f, ssc = a.sc_s ? *a.sc_s : 1.0f;
+    // a warp covers 32 consecutive band points along y (measured faster than
+    // 8 x 4 blocks, whose lanes' windows spread over more lines of G)
     const int jy = bx * 32 + threadIdx.x;
     const int jx = by * 8 + threadIdx.y;
     const bool inside = jx < a.npx && jy < a.npy;
@@ -176,7 +234,7 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
         es_weights(f.x, wx);
         es_weights(f.y, wy);
         if (r0 >= 0 && r0 + kW <= Mx && c0 >= 0 && c0 + kW <= My) {
-            acc = window_sum_inside(G, My, a.Nx, a.Ny, r0, c0, wx, wy);
+            acc = window_sum_inside<false>(G, My, a.Nx, a.Ny, r0, c0, wx, wy);
         } else {  // the window wraps around the periodic grid
             int cols[kW];
 #pragma unroll
@@ -257,7 +315,7 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     es_weights(f.x, wx);
     es_weights(f.y, wy);
     if (r0 >= 0 && r0 + kW <= My && c0 >= 0 && c0 + kW <= Mx) {
-        acc = window_sum_inside(Q, Mx, a.npy, a.npx, r0, c0, wy, wx);
+        acc = window_sum_inside<true>(Q, Mx, a.npy, a.npx, r0, c0, wy, wx);
     } else {  // the window wraps around the periodic grid
         int cols[kW];
 #pragma unroll
@@ -280,6 +338,8 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const long o = (long)j * a.ox + i;
     if (a.kind == 0) {
         ((float *)a.out)[o] = fmaf(acc.x, acc.x, acc.y * acc.y);
+    } else if (a.kind == 2) {  // accumulate |O|^2 (speckle averaging)
+        ((float *)a.out)[o] += fmaf(acc.x, acc.x, acc.y * acc.y);
     } else {
         // e^{i kappa (b + f)^2 / 4} per axis: the b^2 part from the table, the
         // rest, kappa b f / 2 + kappa f^2 / 4, in turns reduced mod 1 exactly:
