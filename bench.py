@@ -121,7 +121,7 @@ def _peaks():
 
 def _traffic(stage):
     """dram bytes per launch of `stage` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+    was taken on the current sources of that kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -129,10 +129,10 @@ def _traffic(stage):
     except (OSError, ValueError):
         return None
     from paper_2410_13474_gb300 import build as b
-    if d.get("sources_sha256") != b.sources_digest():
-        return None
     e = d.get("kernels", {}).get(stage)
-    return None if e is None else e.get("dram_bytes_per_launch")
+    if e is None or e.get("sources_sha256") != b.sources_digest(e.get("sources")):
+        return None
+    return e.get("dram_bytes_per_launch")
 
 
 def cpu_baseline(w, min_seconds=10.0, n=1024):
@@ -347,6 +347,68 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """Focal sweep of the 16K UWA hologram: full 16384^2 intensity views at eight
+    depths in [0.6, 3] m (the paper's 16K object depths).  One sweep call (the
+    stretched band, z-independent, computed once) against the same eight views
+    as single-view calls; views/s and output Mpix/s of each."""
+    import torch
+
+    import paper_2410_13474_gb300 as nf
+    import synth
+    from synth.configs import UWA_16K as w
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2410_13474_gb300 import build as b
+    b.build()
+    depths = [0.6, 0.8, 1.0, 1.3, 1.6, 2.0, 2.5, 3.0]
+    h = synth.gpu_hologram(w.point_cloud(), w.wavelength, w.pitch, w.n, w.n)
+    plan = nf.Plan(w.wavelength, w.pitch, w.n, w.n, h)
+    del h
+    views = [nf.View(z=z) for z in depths]
+    outs = [plan.output_like(v) for v in views]
+    single = [torch.empty_like(o) for o in outs]
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def sweep():
+        _, st = plan.reconstruct_sweep(views, outs)
+        assert all(s == 0 for s in st), st
+
+    def singles():
+        for v, o in zip(views, single):
+            plan.reconstruct(v, o)
+
+    res = {}
+    for name, fn in (("sweep", sweep), ("single_views", singles)):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        k = max(2, args.steps // 8)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / k
+        res[name] = {"ms_per_sweep": round(ms, 3), "ms_per_view": round(ms / len(views), 3),
+                     "views_per_s": round(len(views) / (ms * 1e-3), 2),
+                     "Mpix_per_s": round(len(views) * w.n * w.n / (ms * 1e-3) / 1e6, 2),
+                     "repeats": k}
+    same = all(torch.equal(a, b) for a, b in zip(outs, single))
+    line = {"metric": "focal sweep Mpix/s (16K UWA, 8 depths)", "value": res["sweep"]["Mpix_per_s"],
+            "unit": "Mpix/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "depths_m": depths,
+                       "view": "full %dx%d intensity" % (w.n, w.n),
+                       "step": "hologram loaded once; 8 views (stretch once, FrT + remap per z)"},
+            "sweep": res["sweep"], "single_views": res["single_views"],
+            "speedup": round(res["single_views"]["ms_per_sweep"] / res["sweep"]["ms_per_sweep"], 3),
+            "sweep_equals_single_views_bitwise": bool(same)}
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """Batched workload: 8 holograms of uneven size, 64 partial views of uneven
     size, position and depth.  One batched call (per-stage persistent kernels
@@ -507,11 +569,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uwa16k",
-                    choices=["uwa16k", "wa4096", "small512", "strip16k", "batch64", "serve"])
+                    choices=["uwa16k", "wa4096", "small512", "strip16k", "batch64", "serve", "sweep16k"])
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == "sweep16k":
+        return run_sweep(args)
     if args.workload == "batch64":
         return run_batch(args)
     if args.workload == "serve":

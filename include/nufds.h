@@ -55,6 +55,19 @@ extern "C" {
 
 #define NUFDS_OUT_INTENSITY_F32 0
 #define NUFDS_OUT_FIELD_C64 1
+/* |O|^2 added to the float32 values already in d_out (not overwritten): the
+ * mean intensity over several holograms -- the speckle averaging over
+ * random-phase CGHs of Section 5 -- is K such calls into one zeroed buffer,
+ * then a division by K.  Calls accumulating into one buffer must be ordered
+ * (same stream). */
+#define NUFDS_OUT_INTENSITY_ACCUM_F32 2
+
+/* reconstruction method of a view */
+#define NUFDS_MODE_NUFDS 0     /* the NU-FDS method (stretch, FrT, Eq. 17 remap)          */
+#define NUFDS_MODE_PLAIN_FRT 1 /* Eq. 2 alone at z: no stretch, x' = x_o (the paper's Fig.
+                                * 10b comparison).  Band from the view's own extent; views
+                                * needing N' > 24576 are NUFDS_EUNSUPPORTED; not available
+                                * in nufds_reconstruct_noalloc */
 
 typedef struct nufds_plan nufds_plan;
 
@@ -62,7 +75,7 @@ typedef struct nufds_params {
     double wavelength_m;       /* lambda > 0, lambda < 2 pitch (Eq. 1)                  */
     double pitch_m;            /* hologram pixel pitch Delta                            */
     int32_t nx, ny;            /* hologram size; each a multiple of 4, 16 <= n <= 16384 */
-    int32_t precision;         /* NUFDS_FP32 (only value supported so far)              */
+    int32_t precision;         /* NUFDS_FP32, NUFDS_FP16_STORE or NUFDS_BF16_STORE      */
     int32_t reserved;          /* must be 0                                             */
     uint64_t hbm_budget_bytes; /* cap on device memory the plan may allocate; 0 = none  */
 } nufds_params;
@@ -74,8 +87,8 @@ typedef struct nufds_view {
     double width_m;            /* view size; 0,0 = full view B = 2 z tan(asin(l/2D))    */
     double height_m;
     int32_t out_nx, out_ny;    /* output pixels; 0,0 = N_x, N_y                         */
-    int32_t out_kind;          /* NUFDS_OUT_INTENSITY_F32 or NUFDS_OUT_FIELD_C64        */
-    int32_t reserved;          /* must be 0                                             */
+    int32_t out_kind;          /* NUFDS_OUT_INTENSITY_F32, _FIELD_C64 or _INTENSITY_ACCUM_F32 */
+    int32_t mode;              /* NUFDS_MODE_NUFDS or NUFDS_MODE_PLAIN_FRT              */
 } nufds_view;
 
 /* What the planner decided for one view (Section 4 output grid; band from Eq. 17). */
@@ -143,6 +156,22 @@ int nufds_reconstruct(nufds_plan *plan, const nufds_view *view, void *d_out, voi
 int nufds_reconstruct_batch(nufds_plan *const *plans, const nufds_view *views,
                             void *const *d_outs, int32_t count, void *cuda_stream,
                             int32_t *statuses);
+
+/*
+ * Focal sweep (several depths, or several views, of one loaded hologram).
+ * Section 4: the magnification m(f) does not depend on z, so the pull-back of
+ * the stretched lattice and therefore the stretched spectrum S of a band
+ * depend only on the band (its bounds and centre) and N'.  Views are
+ * reconstructed in order; a view whose band and N' equal those of the
+ * previous successful view reuses its S and runs only the Fresnel transform
+ * at its own z (Eq. 2) and the output remap (Eq. 17).  Full views at the
+ * paper's depths (0.5-3 m) all share one band.  Results are bitwise those of
+ * nufds_reconstruct.  The workspace holds one extra N'_x N'_y array (S).
+ * views[i] -> d_outs[i] as in nufds_reconstruct, on cuda_stream; statuses (may
+ * be NULL) receives one code per view.  Returns NUFDS_OK or the first error.
+ */
+int nufds_reconstruct_sweep(nufds_plan *plan, const nufds_view *views, void *const *d_outs,
+                            int32_t count, void *cuda_stream, int32_t *statuses);
 
 /* Free the plan and its device memory (synchronises its streams).  NULL-safe. */
 void nufds_destroy(nufds_plan *plan);

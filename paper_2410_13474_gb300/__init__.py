@@ -20,11 +20,12 @@ LIB_PATH = os.path.join(_HERE, "libnufds.so")
 
 OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 FP32, FP16_STORE, BF16_STORE = 0, 1, 2
-OUT_INTENSITY, OUT_FIELD = 0, 1
+OUT_INTENSITY, OUT_FIELD, OUT_INTENSITY_ACCUM = 0, 1, 2
+MODE_NUFDS, MODE_PLAIN_FRT = 0, 1
 
 # every function include/nufds.h declares
 ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",
-                 "nufds_reconstruct_batch", "nufds_destroy", "nufds_plan_device_bytes",
+                 "nufds_reconstruct_batch", "nufds_reconstruct_sweep", "nufds_destroy", "nufds_plan_device_bytes",
                  "nufds_status_string", "nufds_launch_count", "nufds_profile",
                  "nufds_profile_read", "nufds_reconstruct_noalloc")
 
@@ -46,7 +47,7 @@ class _View(ctypes.Structure):
                 ("center_y_m", ctypes.c_double), ("width_m", ctypes.c_double),
                 ("height_m", ctypes.c_double), ("out_nx", ctypes.c_int32),
                 ("out_ny", ctypes.c_int32), ("out_kind", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("mode", ctypes.c_int32)]
 
 
 class _ViewInfo(ctypes.Structure):
@@ -86,6 +87,8 @@ def lib():
         L.nufds_reconstruct_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_View),
                                               ctypes.POINTER(vp), ctypes.c_int32, vp,
                                               ctypes.POINTER(ctypes.c_int32)]
+        L.nufds_reconstruct_sweep.argtypes = [vp, ctypes.POINTER(_View), ctypes.POINTER(vp),
+                                              ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_int32)]
         L.nufds_destroy.argtypes = [vp]
         L.nufds_destroy.restype = None
         L.nufds_plan_device_bytes.argtypes = [vp]
@@ -127,10 +130,11 @@ class View:
     out_nx: int = 0
     out_ny: int = 0
     kind: int = OUT_INTENSITY
+    mode: int = MODE_NUFDS          # MODE_PLAIN_FRT: Eq. 2 alone (no stretch, x' = x_o)
 
     def _c(self) -> _View:
         return _View(self.z, self.center_x, self.center_y, self.width, self.height,
-                     self.out_nx, self.out_ny, self.kind, 0)
+                     self.out_nx, self.out_ny, self.kind, self.mode)
 
 
 def _params(wavelength, pitch, nx, ny, precision=FP32, budget=0) -> _Params:
@@ -184,20 +188,33 @@ class Plan:
     def output_like(self, view: View):
         import torch
         info = self.view_plan(view)
-        dt = torch.float32 if view.kind == OUT_INTENSITY else torch.complex64
+        dt = torch.complex64 if view.kind == OUT_FIELD else torch.float32
         return torch.empty((info["out_ny"], info["out_nx"]), dtype=dt, device="cuda")
 
     def reconstruct(self, view: View, out=None, stream=None):
         import torch
         if out is None:
             out = self.output_like(view)
-        want = torch.float32 if view.kind == OUT_INTENSITY else torch.complex64
+        want = torch.complex64 if view.kind == OUT_FIELD else torch.float32
         if not (out.is_cuda and out.dtype == want and out.is_contiguous()):
             raise ValueError("out must be a contiguous cuda %s tensor" % want)
         v = view._c()
         _check(lib().nufds_reconstruct(self._p, ctypes.byref(v), ctypes.c_void_p(out.data_ptr()),
                                        _stream_handle(stream)), "nufds_reconstruct")
         return out
+
+    def reconstruct_sweep(self, views, outs=None, stream=None):
+        """Views of the loaded hologram in order (e.g. a focal sweep over z); a view
+        with the band and N' of the previous one reuses its stretched spectrum.
+        Returns (outs, per-view status codes)."""
+        if outs is None:
+            outs = [self.output_like(v) for v in views]
+        n = len(views)
+        va = (_View * n)(*[v._c() for v in views])
+        oa = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        st = (ctypes.c_int32 * n)()
+        lib().nufds_reconstruct_sweep(self._p, va, oa, n, _stream_handle(stream), st)
+        return outs, list(st)
 
     def profile(self, enable: bool = True):
         """Start (clearing) or stop recording CUDA events around every launch."""

@@ -78,12 +78,14 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
 
 
 
-def sources_digest() -> str:
-    """sha256 over the CUDA sources and headers (ties profiles to the code they measured)."""
+def sources_digest(files=None) -> str:
+    """sha256 over CUDA sources and headers (all, or the named files of csrc/):
+    ties a profile to the code it measured."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh")))
-    for f in files:
+    if files is None:
+        files = [f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
+    for f in sorted(files):
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()

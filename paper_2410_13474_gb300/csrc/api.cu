@@ -26,6 +26,11 @@
 
 namespace nufds {
 
+static bool kind_ok(int k) {
+    return k == NUFDS_OUT_INTENSITY_F32 || k == NUFDS_OUT_FIELD_C64 ||
+           k == NUFDS_OUT_INTENSITY_ACCUM_F32;
+}
+
 static thread_local int64_t t_launches = 0;
 
 // With NUFDS_DEBUG set, report the CUDA error behind an NUFDS_ECUDA return.
@@ -50,12 +55,13 @@ struct ViewPlan {
     int npx, npy;
     double px, py, w, h, z, cx, cy;
     bool lattice;
+    bool plain;  // NUFDS_MODE_PLAIN_FRT
     long i0, j0;
 };
 
 struct ViewKey {
     double z, cx, cy, w, h;
-    int ox, oy;
+    int ox, oy, mode, pad;
     bool operator==(const ViewKey &o) const { return memcmp(this, &o, sizeof(ViewKey)) == 0; }
 };
 
@@ -153,9 +159,11 @@ struct Geom {
 };
 
 static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
-    if (!v || !(v->z_m > 0) || v->reserved != 0) return NUFDS_EINVAL;
-    if (v->out_kind != NUFDS_OUT_INTENSITY_F32 && v->out_kind != NUFDS_OUT_FIELD_C64)
+    if (!v || !(v->z_m > 0)) return NUFDS_EINVAL;
+    if (v->mode != NUFDS_MODE_NUFDS && v->mode != NUFDS_MODE_PLAIN_FRT) return NUFDS_EINVAL;
+    if (!kind_ok(v->out_kind))
         return NUFDS_EINVAL;
+    o->plain = v->mode == NUFDS_MODE_PLAIN_FRT;
     const double lam = P->lam, pitch = P->pitch, z = v->z_m;
     double w = v->width_m, h = v->height_m;
     const double B = full_width(lam, pitch, z);
@@ -187,15 +195,23 @@ static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
     // horizontal one (and x <-> y for k_y).  The extremes over the boundary are
     // therefore at the corners or at the edge pixels nearest the axes; those
     // candidates give the same min/max as evaluating every boundary pixel.
+    // (The plain Fresnel transform maps x' = x_o: the extremes are corners.)
     double kmin[2] = {1e300, 1e300}, kmax[2] = {-1e300, -1e300};
     auto eval = [&](int i, int j) {
         i = i < 0 ? 0 : (i >= ox ? ox - 1 : i);
         j = j < 0 ? 0 : (j >= oy ? oy - 1 : j);
         double xo = o->cx + (i - 0.5 * ox) * o->px, yo = o->cy + (j - 0.5 * oy) * o->py;
-        double R0 = sqrt(xo * xo + yo * yo + z * z);
-        double up, vp;
-        host_phi(xo / R0, yo / R0, &up, &vp);
-        double kx = P->nx * pitch * up / lam, ky = P->ny * pitch * vp / lam;
+        double kx, ky;
+        if (o->plain) {
+            kx = xo * P->nx * pitch / (lam * z);
+            ky = yo * P->ny * pitch / (lam * z);
+        } else {
+            double R0 = sqrt(xo * xo + yo * yo + z * z);
+            double up, vp;
+            host_phi(xo / R0, yo / R0, &up, &vp);
+            kx = P->nx * pitch * up / lam;
+            ky = P->ny * pitch * vp / lam;
+        }
         kmin[0] = fmin(kmin[0], kx);
         kmax[0] = fmax(kmax[0], kx);
         kmin[1] = fmin(kmin[1], ky);
@@ -230,7 +246,7 @@ static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
     // pixels on the full view's lattice?  (then the plan's output-map table serves)
     const double fpx = B / P->nx, fpy = B / P->ny;
     o->lattice = false;
-    if (fabs(o->px - fpx) <= 1e-12 * fpx && fabs(o->py - fpy) <= 1e-12 * fpy) {
+    if (!o->plain && fabs(o->px - fpx) <= 1e-12 * fpx && fabs(o->py - fpy) <= 1e-12 * fpy) {
         double ri = o->cx / fpx - 0.5 * ox + 0.5 * P->nx;
         double rj = o->cy / fpy - 0.5 * oy + 0.5 * P->ny;
         double ii = rint(ri), jj = rint(rj);
@@ -254,13 +270,12 @@ static int plan_view_cached(nufds_plan *P, const nufds_view *v, ViewPlan *o) {
     key.h = v->height_m;
     key.ox = v->out_nx;
     key.oy = v->out_ny;
+    key.mode = v->mode;
     for (auto it = P->vcache.begin(); it != P->vcache.end(); ++it)
         if (it->first == key) {
             *o = it->second;
             P->vcache.splice(P->vcache.begin(), P->vcache, it);
-            return v->out_kind == NUFDS_OUT_INTENSITY_F32 || v->out_kind == NUFDS_OUT_FIELD_C64
-                       ? NUFDS_OK
-                       : NUFDS_EINVAL;
+            return kind_ok(v->out_kind) ? NUFDS_OK : NUFDS_EINVAL;
         }
     Geom g = {P->lam, P->pitch, P->nx, P->ny};
     int rc = plan_view_impl(&g, v, o);
@@ -273,14 +288,14 @@ static int plan_view_cached(nufds_plan *P, const nufds_view *v, ViewPlan *o) {
 // Workspace layout of one view (bytes): A (Q and the first pass output),
 // B (S and the transposed pass input), scratch of the view passes, tables.
 struct ViewWs {
-    size_t A, B, scr, chirp, outc, rm, total;
+    size_t A, B, scr, chirp, outc, rm, keep, total;
     int grid_y, grid_x;
     long ex_b0, ey_b0;
     int nbx, nby;
 };
 
 static int view_ws(const nufds_plan *P, const ViewPlan &V, const FftPlan *fpx, const FftPlan *fpy,
-                   int kind, ViewWs *w) {
+                   int kind, ViewWs *w, bool keep_band = false) {
     const size_t np = (size_t)V.npx * V.npy, eb = prec_bytes(P->prec);
     w->A = align256(eb * 4 * np);
     w->B = align256(eb * 2 * np);
@@ -295,7 +310,10 @@ static int view_ws(const nufds_plan *P, const ViewPlan &V, const FftPlan *fpx, c
     w->nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
     w->outc = kind == NUFDS_OUT_FIELD_C64 ? align256(sizeof(OutChirp) * (w->nbx + w->nby)) : 0;
     w->rm = V.lattice ? 0 : align256((sizeof(short2) + sizeof(uint2)) * (size_t)V.ox * V.oy + 256);
-    w->total = w->A + w->B + w->scr + w->chirp + w->outc + w->rm;
+    // a focal sweep keeps the stretched band (S_T) apart from B, which the
+    // Fresnel passes of each depth overwrite
+    w->keep = keep_band ? align256(eb * np) : 0;
+    w->total = w->A + w->B + w->scr + w->chirp + w->outc + w->rm + w->keep;
     (void)P;
     return NUFDS_OK;
 }
@@ -372,7 +390,35 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
     return NUFDS_OK;
 }
 
-static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cudaStream_t st) {
+// Stretched band kept across the views of a focal sweep: the pull-back and
+// the band depend on the geometry, not on z (Section 4: m is independent of
+// z), so views with the same band, band centre and N' share S.
+struct Sweep {
+    bool valid = false;
+    long klo_x, khi_x, klo_y, khi_y, kc_x, kc_y;
+    int npx, npy;
+    bool plain;
+    bool same(const ViewPlan &V) const {
+        return valid && plain == V.plain && klo_x == V.klo_x && khi_x == V.khi_x && klo_y == V.klo_y &&
+               khi_y == V.khi_y && kc_x == V.kc_x && kc_y == V.kc_y && npx == V.npx &&
+               npy == V.npy;
+    }
+    void set(const ViewPlan &V) {
+        valid = true;
+        plain = V.plain;
+        klo_x = V.klo_x;
+        khi_x = V.khi_x;
+        klo_y = V.klo_y;
+        khi_y = V.khi_y;
+        kc_x = V.kc_x;
+        kc_y = V.kc_y;
+        npx = V.npx;
+        npy = V.npy;
+    }
+};
+
+static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cudaStream_t st,
+                            Sweep *sw = nullptr) {
     if (!P || !v || !d_out) return NUFDS_EINVAL;
     if (!P->loaded) return NUFDS_EINVAL;
     int rc;
@@ -380,14 +426,15 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return NUFDS_EINVAL;
     ViewPlan V;
     if ((rc = plan_view_cached(P, v, &V))) return rc;
-    if (V.klo_x < P->pb_kx0 || V.khi_x >= P->pb_kx0 + P->pb_nkx || V.klo_y < P->pb_ky0 ||
-        V.khi_y >= P->pb_ky0 + P->pb_nky)
+    if (!V.plain && (V.klo_x < P->pb_kx0 || V.khi_x >= P->pb_kx0 + P->pb_nkx ||
+                     V.klo_y < P->pb_ky0 || V.khi_y >= P->pb_ky0 + P->pb_nky))
         return NUFDS_EUNSUPPORTED;
     const FftPlan *fpx, *fpy;
     if ((rc = fft_plan_get(V.npx, &fpx))) return rc;
     if ((rc = fft_plan_get(V.npy, &fpy))) return rc;
     ViewWs W;
-    view_ws(P, V, fpx, fpy, v->out_kind, &W);
+    view_ws(P, V, fpx, fpy, v->out_kind, &W, sw != nullptr);
+    if (sw && W.total > P->ws_bytes) sw->valid = false;  // the workspace moves
     if ((rc = ensure_ws(P, W.total))) return rc;
     char *p = P->ws;
     void *A = p;
@@ -398,6 +445,8 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     p += W.scr;
     float2 *chx = (float2 *)p, *chy = chx + V.npx;
     p += W.chirp;
+    void *S = W.keep ? (void *)p : Bf;  // where the stretch writes S_T
+    p += W.keep;
     OutChirp *Ex = (OutChirp *)p, *Ey = Ex + W.nbx;
     p += W.outc;
     short2 *rmb = P->rm_base;
@@ -412,7 +461,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
         rm_ld = V.ox;
         if ((rc = stage(P, ST_TABLES, 12.0 * V.ox * V.oy, st, [&] {
                  return launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px,
-                                           V.py, V.ox, V.oy, rmb, rmf, st);
+                                           V.py, V.ox, V.oy, rmb, rmf, st, V.plain);
              })))
             return rc;
     }
@@ -453,30 +502,35 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     sa.kc_y = V.kc_y;
     sa.npx = V.npx;
     sa.npy = V.npy;
-    sa.S = Bf;
+    sa.S = S;
+    sa.plain = V.plain;
     sa.prec = P->prec;
     sa.sc_g = scale_ptr(P, 1);
     sa.sc_s = scale_ptr(P, 2);
     sa.energy = P->prec == NUFDS_FP16_STORE ? P->acc + 2 : nullptr;
     const double np2 = (double)V.npx * V.npy, q = prec_bytes(P->prec) / 8.0;
     const double nbx = (double)(V.khi_x - V.klo_x + 1), nby = (double)(V.khi_y - V.klo_y + 1);
-    if (P->prec == NUFDS_FP16_STORE &&
-        cudaMemsetAsync(P->acc + 2, 0, sizeof(double), st) != cudaSuccess)
-        return NUFDS_ECUDA;
     // algorithmic bytes of the gather: table entries of the band, the part of
     // G the band pulls back to (in proportion to the full band), S written
     const double g_frac = (nbx * nby) / ((double)P->pb_nkx * P->pb_nky);
     const double st_bytes = 12.0 * nbx * nby + 32.0 * q * P->nx * P->ny * g_frac + 8.0 * q * np2;
-    if ((rc = stage(P, ST_STRETCH, st_bytes, st, [&] { return launch_stretch(sa, st); })))
-        return rc;
-    if (P->prec == NUFDS_FP16_STORE &&
-        (rc = stage(P, ST_TABLES, 0.0, st, [&] {
-             return launch_scales_view(P->sc, P->acc, fpx->dmax, fpy->dmax, st);
-         })))
-        return rc;
+    if (!(sw && sw->same(V))) {  // a sweep reuses the band of an earlier depth
+        if (P->prec == NUFDS_FP16_STORE &&
+            cudaMemsetAsync(P->acc + 2, 0, sizeof(double), st) != cudaSuccess)
+            return NUFDS_ECUDA;
+        if ((rc = stage(P, ST_STRETCH, st_bytes, st, [&] { return launch_stretch(sa, st); })))
+            return rc;
+        // the FP16 scales of S and of the passes depend on S's energy only
+        if (P->prec == NUFDS_FP16_STORE &&
+            (rc = stage(P, ST_TABLES, 0.0, st, [&] {
+                 return launch_scales_view(P->sc, P->acc, fpx->dmax, fpy->dmax, st);
+             })))
+            return rc;
+        if (sw) sw->set(V);
+    }
     // steps two/three along y: S_T rows (npx of npy) -> A (npx x 2npy)
     if ((rc = stage(P, ST_VIEW_ROWS_Y, 24.0 * q * np2, st, [&] {
-             return launch_rows_view(*fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y,
+             return launch_rows_view(*fpy, S, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y,
                                      P->prec, scale_ptr(P, 2), scale_ptr(P, 3), st);
          })))
         return rc;
@@ -517,7 +571,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ra.sc_q = scale_ptr(P, 5);
     // Q region the view maps into, its table, the output
     const double rm_bytes = 32.0 * q * nbx * nby + 12.0 * V.ox * V.oy +
-                            (v->out_kind == NUFDS_OUT_FIELD_C64 ? 8.0 : 4.0) * V.ox * V.oy;
+                            (v->out_kind == NUFDS_OUT_INTENSITY_F32 ? 4.0 : 8.0) * V.ox * V.oy;
     return stage(P, ST_REMAP, rm_bytes, st, [&] { return launch_remap(ra, st); });
 }
 
@@ -595,10 +649,13 @@ static size_t view_batch_bytes(const BatchView &b, int prec) {
     return t;
 }
 
+// FFT-length classes of the batched row passes (L <= 1024, 2048, .., larger)
+constexpr int kRowClasses = 6;
+
 static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_t *statuses) {
     // ---- sizes and the workspace
     int maxL = 0, threads = 64;
-    size_t smem = 0, views_bytes = 0;
+    size_t scr_elems = 0, views_bytes = 0;
     std::vector<const FftPlan *> fps;
     auto fidx = [&](const FftPlan *f) {
         for (size_t i = 0; i < fps.size(); ++i)
@@ -606,27 +663,55 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         fps.push_back(f);
         return (int)fps.size() - 1;
     };
-    int rows_y = 0, rows_x = 0;
     for (auto &b : w) {
-        for (const FftPlan *f : {b.fpx, b.fpy}) {
-            maxL = std::max(maxL, f->L);
-            threads = std::max(threads, f->threads);
-            smem = std::max(smem, f->smem_bytes);
-            fidx(f);
-        }
+        for (const FftPlan *f : {b.fpx, b.fpy}) fidx(f);
         b.off = views_bytes;
         b.bytes = view_batch_bytes(b, prec);
         views_bytes += b.bytes;
-        rows_y += b.V.npx;
-        rows_x += 2 * b.V.npy;
     }
     const int n = (int)w.size();
-    const int grid = rows_view_batch_grid(threads, smem, std::max(rows_y, rows_x));
-    const size_t scr_bytes = align256(sizeof(float2) * (size_t)grid * maxL);
+    // Row items of each pass grouped by FFT-length class (L <= 1024, 2048, ..):
+    // one launch per class with that class's shared memory, block size and
+    // grid, so short rows are not run at the occupancy of the longest.
+    auto len_class = [](int L) {
+        int c = 0;
+        while (c < kRowClasses - 1 && L > (1024 << c)) ++c;
+        return c;
+    };
+    struct RowClass {
+        int first = 0, count = 0, rows = 0, threads = 64, maxL = 0, grid = 0;
+        size_t smem = 0;
+    };
+    RowClass cls[2][kRowClasses];
+    std::vector<int> order[2];  // view indices of the y and x items, by class
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int c = 0; c < kRowClasses; ++c) {
+            RowClass &rc = cls[pass][c];
+            rc.first = (int)order[pass].size();
+            for (int i = 0; i < n; ++i) {
+                const FftPlan *f = pass == 0 ? w[i].fpy : w[i].fpx;
+                if (len_class(f->L) != c) continue;
+                order[pass].push_back(i);
+                rc.count++;
+                rc.rows += pass == 0 ? w[i].V.npx : 2 * w[i].V.npy;
+                rc.threads = std::max(rc.threads, std::min(512, f->threads));
+                rc.maxL = std::max(rc.maxL, f->L);
+                rc.smem = std::max(rc.smem, f->smem_bytes);
+            }
+            if (rc.count) {
+                rc.grid = rows_view_batch_grid(rc.threads, rc.smem, rc.rows);
+                maxL = std::max(maxL, rc.maxL);
+                threads = std::max(threads, rc.threads);
+                scr_elems = std::max(scr_elems, (size_t)rc.grid * rc.maxL);
+            }
+        }
+    }
+    const size_t scr_bytes = align256(sizeof(float2) * scr_elems);
     // descriptors: PassArgs[], RowItem[2n], row offsets, TrItem[n], tile offsets,
     // StretchArgs[n], RemapArgs[n], offsets
     const size_t desc_bytes = align256(sizeof(PassArgs) * fps.size()) +
-                              align256(sizeof(RowItem) * 2 * n) + align256(sizeof(int) * 2 * (n + 1)) +
+                              align256(sizeof(RowItem) * 2 * n) +
+                              align256(sizeof(int) * 2 * (n + kRowClasses)) +
                               align256(sizeof(TrItem) * n) + align256(sizeof(int) * (n + 1)) +
                               align256(sizeof(StretchArgs) * n) + align256(sizeof(int) * (n + 1)) +
                               align256(sizeof(RemapArgs) * n) + align256(sizeof(int) * (n + 1));
@@ -674,7 +759,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
     size_t o = 0;
     auto carve = [&](size_t bytes) { size_t r = o; o += align256(bytes); return r; };
     const size_t o_pa = carve(sizeof(PassArgs) * fps.size()), o_ri = carve(sizeof(RowItem) * 2 * n),
-                 o_roff = carve(sizeof(int) * 2 * (n + 1)), o_tr = carve(sizeof(TrItem) * n),
+                 o_roff = carve(sizeof(int) * 2 * (n + kRowClasses)),
+                 o_tr = carve(sizeof(TrItem) * n),
                  o_toff = carve(sizeof(int) * (n + 1)), o_sa = carve(sizeof(StretchArgs) * n),
                  o_soff = carve(sizeof(int) * (n + 1)), o_ra = carve(sizeof(RemapArgs) * n),
                  o_roff2 = carve(sizeof(int) * (n + 1));
@@ -701,7 +787,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         int nbx, nby;
     };
     std::vector<Regions> R(n);
-    int ty = 0, tx = 0, ttr = 0, tst = 0, trm = 0;
+    std::vector<RowItem> items_y(n), items_x(n);
+    int ttr = 0, tst = 0, trm = 0;
     for (int i = 0; i < n; ++i) {
         BatchView &b = w[i];
         const ViewPlan &V = b.V;
@@ -763,13 +850,14 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         sa.npx = V.npx;
         sa.npy = V.npy;
         sa.S = g.Bf;
+        sa.plain = V.plain;
         sa.prec = prec;
         sa.sc_g = scG;
         sa.sc_s = scS;
         sa.energy = prec == NUFDS_FP16_STORE ? g.acc + 2 : nullptr;
         hsoff[i] = tst;
         tst += stretch_tiles(V.npx, V.npy);
-        RowItem &ry = hri[i];
+        RowItem &ry = items_y[i];
         ry.in = g.Bf;
         ry.out = g.A;
         ry.chirp = g.chy;
@@ -778,9 +866,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         ry.args = fidx(b.fpy);
         ry.sc_in = scS;
         ry.sc_out = scT;
-        hroff[i] = ty;
-        ty += V.npx;
-        RowItem &rx = hri[n + i];
+        RowItem &rx = items_x[i];
         rx.in = g.Bf;
         rx.out = g.A;
         rx.chirp = g.chx;
@@ -789,8 +875,6 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         rx.args = fidx(b.fpx);
         rx.sc_in = scT;
         rx.sc_out = scQ;
-        hroff[n + 1 + i] = tx;
-        tx += 2 * V.npy;
         TrItem &tr = htr[i];
         tr.in = g.A;
         tr.out = g.Bf;
@@ -827,8 +911,25 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         hrmoff[i] = trm;
         trm += remap_tiles(V.ox, V.oy);
     }
-    hroff[n] = ty;
-    hroff[2 * n + 1] = tx;
+    // row items in class order; per class an offsets array starting at 0
+    int *coff[2][kRowClasses];
+    {
+        int k = 0, off = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int c = 0; c < kRowClasses; ++c) {
+                RowClass &rc = cls[pass][c];
+                coff[pass][c] = hroff + off;
+                int rows = 0;
+                for (int q = 0; q < rc.count; ++q) {
+                    const int i = order[pass][rc.first + q];
+                    hri[k++] = pass == 0 ? items_y[i] : items_x[i];
+                    hroff[off++] = rows;
+                    rows += pass == 0 ? w[i].V.npx : 2 * w[i].V.npy;
+                }
+                hroff[off++] = rows;
+            }
+        }
+    }
     htoff[n] = ttr;
     hsoff[n] = tst;
     hrmoff[n] = trm;
@@ -879,7 +980,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
             }
             if (!rc && !V.lattice)
                 rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px, V.py,
-                                        V.ox, V.oy, g.rmb, g.rmf, st);
+                                        V.ox, V.oy, g.rmb, g.rmf, st, V.plain);
             if (!rc && prec == NUFDS_FP16_STORE &&
                 cudaMemsetAsync(g.acc, 0, 4 * sizeof(double), st) != cudaSuccess)
                 rc = NUFDS_ECUDA;
@@ -890,15 +991,23 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
                                       (const int *)(ddesc + o_soff), n, tst, prec, st);
         for (int i = 0; i < n && !rc && prec == NUFDS_FP16_STORE; ++i)
             rc = launch_scales_view(R[i].sc, R[i].acc, w[i].fpx->dmax, w[i].fpy->dmax, st);
-        if (!rc && (where = "rows_y"))
-            rc = launch_rows_view_batch(dpa, dri, droff, n, ty, threads, smem,
-                                        (float2 *)scr_base, maxL, grid, prec, st);
+        auto rows_pass = [&](int pass) {
+            int r = 0, item0 = pass == 0 ? 0 : n;
+            for (int c = 0; c < kRowClasses && !r; ++c) {
+                const RowClass &k = cls[pass][c];
+                if (!k.count) continue;
+                r = launch_rows_view_batch(dpa, dri + item0 + k.first,
+                                           droff + (coff[pass][c] - hroff), k.count, k.rows,
+                                           k.threads, k.smem, (float2 *)scr_base, k.maxL,
+                                           k.grid, prec, st);
+            }
+            return r;
+        };
+        if (!rc && (where = "rows_y")) rc = rows_pass(0);
         if (!rc && (where = "transpose"))
             rc = launch_transpose_batch((const TrItem *)(ddesc + o_tr),
                                         (const int *)(ddesc + o_toff), n, ttr, prec, st);
-        if (!rc && (where = "rows_x"))
-            rc = launch_rows_view_batch(dpa, dri + n, droff + n + 1, n, tx, threads, smem,
-                                        (float2 *)scr_base, maxL, grid, prec, st);
+        if (!rc && (where = "rows_x")) rc = rows_pass(1);
         if (!rc && (where = "remap"))
             rc = launch_remap_batch((const RemapArgs *)(ddesc + o_ra),
                                     (const int *)(ddesc + o_roff2), n, trm, prec, st);
@@ -906,8 +1015,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         if (rc || ce != cudaSuccess) {
             if (ce == cudaSuccess) cudaGraphDestroy(graph);
             if (getenv("NUFDS_DEBUG"))
-                fprintf(stderr, "nufds: batch capture stage %s (threads %d smem %zu grid %d)\n",
-                        where, threads, smem, grid);
+                fprintf(stderr, "nufds: batch capture stage %s (max threads %d, max L %d)\n",
+                        where, threads, maxL);
             int r2 = CUDA_FAIL(rc ? "a launch during capture" : "cudaStreamEndCapture");
             return rc ? rc : r2;
         }
@@ -950,8 +1059,9 @@ static int batch_impl(nufds_plan *const *plans, const nufds_view *views, void *c
         b.kind = views[i].out_kind;
         b.out = outs[i];
         int rc = plan_view_cached(P, &views[i], &b.V);
-        if (!rc && (b.V.klo_x < P->pb_kx0 || b.V.khi_x >= P->pb_kx0 + P->pb_nkx ||
-                    b.V.klo_y < P->pb_ky0 || b.V.khi_y >= P->pb_ky0 + P->pb_nky))
+        if (!rc && !b.V.plain &&
+            (b.V.klo_x < P->pb_kx0 || b.V.khi_x >= P->pb_kx0 + P->pb_nkx ||
+             b.V.klo_y < P->pb_ky0 || b.V.khi_y >= P->pb_ky0 + P->pb_nky))
             rc = NUFDS_EUNSUPPORTED;
         if (!rc) rc = fft_plan_get(b.V.npx, &b.fpx);
         if (!rc) rc = fft_plan_get(b.V.npy, &b.fpy);
@@ -1129,6 +1239,20 @@ int nufds_reconstruct(nufds_plan *P, const nufds_view *v, void *d_out, void *str
     return reconstruct_impl(P, v, d_out, (cudaStream_t)stream);
 }
 
+int nufds_reconstruct_sweep(nufds_plan *P, const nufds_view *views, void *const *d_outs,
+                            int32_t count, void *stream, int32_t *statuses) {
+    if (!P || count < 0 || (count > 0 && (!views || !d_outs))) return NUFDS_EINVAL;
+    Sweep sw;
+    int first = NUFDS_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        const int rc = reconstruct_impl(P, &views[i], d_outs[i], (cudaStream_t)stream, &sw);
+        if (rc) sw.valid = false;
+        if (statuses) statuses[i] = rc;
+        if (rc && first == NUFDS_OK) first = rc;
+    }
+    return first;
+}
+
 int nufds_reconstruct_batch(nufds_plan *const *plans, const nufds_view *views,
                             void *const *d_outs, int32_t count, void *stream, int32_t *statuses) {
     if (count < 0 || (count > 0 && (!plans || !views || !d_outs))) return NUFDS_EINVAL;
@@ -1264,6 +1388,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     int rc;
     if ((rc = plan_view_impl(&g, &fv, &F))) return rc;
     if ((rc = plan_view_impl(&g, v, &V))) return rc;
+    if (V.plain) return NUFDS_EUNSUPPORTED;
     if (V.npx > kNoAllocMaxNp || V.npy > kNoAllocMaxNp) return NUFDS_EUNSUPPORTED;
     if (!V.lattice && (long)V.ox * V.oy > kNoAllocMaxOutPix) return NUFDS_EUNSUPPORTED;
     const long pb_kx0 = F.klo_x, pb_ky0 = F.klo_y;
@@ -1365,6 +1490,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     sa.sc_g = nullptr;
     sa.sc_s = nullptr;
     sa.energy = nullptr;
+    sa.plain = 0;
     if ((rc = launch_stretch(sa, st)) ||
         (rc = launch_rows_view(fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, grid_y, PREC_F32,
                                nullptr, nullptr, st)) ||

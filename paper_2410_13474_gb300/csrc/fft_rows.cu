@@ -432,8 +432,9 @@ __global__ void __launch_bounds__(512) k_rows_view(PassArgs P, const T *__restri
 }
 
 // Batched view pass over rows of many items (views, passes) of uneven length:
-// a persistent grid walks the flattened row list; the CTA reloads the pass
-// structure and twiddle tables when it moves to another item.
+// a persistent grid walks the flattened row list (strided: contiguous chunks
+// measured slower, rows of one length class still differ in length); the CTA
+// reloads the pass structure and twiddle tables when it moves to another item.
 template <class T>
 __global__ void __launch_bounds__(512) k_rows_view_batch(const PassArgs *__restrict__ args,
                                                          const RowItem *__restrict__ items,

@@ -218,11 +218,18 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
     short2 b = make_short2(0, 0);
     float2 f = make_float2(0.f, 0.f);
     if (inside && kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
-        const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
-        b = a.pb_base[t];
-        if (b.x != kMasked) {
-            f = a.pb_frac[t];
-            valid = true;
+        if (a.plain) {  // f = f'_k: fine position 2k, zero outside |f| <= 1/(2 pitch)
+            if (2 * labs(kx) <= a.Nx && 2 * labs(ky) <= a.Ny) {
+                b = make_short2((short)(2 * kx), (short)(2 * ky));
+                valid = true;
+            }
+        } else {
+            const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
+            b = a.pb_base[t];
+            if (b.x != kMasked) {
+                f = a.pb_frac[t];
+                valid = true;
+            }
         }
     }
     const int Mx = 2 * a.Nx, My = 2 * a.Ny;

@@ -188,9 +188,10 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
 // the fraction 2t' - b in 0.32 fixed point (exact to 2^-32 of a fine cell:
 // the output chirp changes by up to thousands of radians per fine cell at
 // the paper's depths, so an FP32 fraction would cost 1e-4 rad).
+// plain = 1: the identity map x' = x_o of the plain Fresnel transform instead.
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
                        double px, double py, int ox, int oy, short2 *base, uint2 *frac,
-                       cudaStream_t st);
+                       cudaStream_t st, int plain = 0);
 // chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L at n = natural index of the
 // slot (digit-reversed order of plan fp), x_n = (n - L/2) window / L
 int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,
@@ -230,6 +231,7 @@ struct StretchArgs {
     int prec;               // storage of G and S
     const float *sc_g, *sc_s;
     double *energy;         // if not null: += sum |S|^2 (before storage rounding)
+    int plain;              // 1: no stretch, S(f'_k) = DTFT at f = f'_k (plain FrT)
 };
 int launch_stretch(const StretchArgs &a, cudaStream_t st);
 // batched: item i owns blocks [off[i], off[i+1]) of a 1-D grid (32 x 8 tiles)
@@ -245,7 +247,7 @@ struct RemapArgs {
     const uint2 *rm_frac;   // its fractions, 0.32 fixed point
     long rm_ld, rm_i0, rm_j0;
     int ox, oy;
-    int kind;               // 0 intensity f32, 1 field c64
+    int kind;               // 0 intensity f32, 1 field c64, 2 intensity f32 added to out
     const OutChirp *Ex, *Ey;  // output chirp tables (field only)
     long ex_b0, ey_b0;
     uint2 k2x, k2y;           // kappa / (8 pi) turns, 32.32 fixed point (low, high)

@@ -176,14 +176,19 @@ __device__ inline void split_fine_fx(double t2, short *base, unsigned int *frac)
 // f_0 = (x_o, y_o) / (lambda R_0), for view pixels; layout [j][i].
 __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z, double cx,
                               double cy, double px, double py, int ox, int oy, double g1,
-                              short2 *base, uint2 *frac) {
+                              short2 *base, uint2 *frac, int plain) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)ox * oy) return;
     int j = (int)(idx / ox), i = (int)(idx - (long)j * ox);
     double xo = cx + (i - 0.5 * ox) * px, yo = cy + (j - 0.5 * oy) * py;
-    double R0 = sqrt(xo * xo + yo * yo + z * z);
     double up, vp;
-    phi_uv(xo / R0, yo / R0, g1, &up, &vp);
+    if (plain) {  // x' = x_o: lambda f' = x_o / z
+        up = xo / z;
+        vp = yo / z;
+    } else {
+        double R0 = sqrt(xo * xo + yo * yo + z * z);
+        phi_uv(xo / R0, yo / R0, g1, &up, &vp);
+    }
     double tx = nx * pitch * up / lam, ty = ny * pitch * vp / lam;
     short2 b;
     uint2 f;
@@ -239,11 +244,11 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
 
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
                        double px, double py, int ox, int oy, short2 *base, uint2 *frac,
-                       cudaStream_t st) {
+                       cudaStream_t st, int plain) {
     long n = (long)ox * oy;
     if (n <= 0) return 0;
     k_remap_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lam, pitch, nx, ny, z, cx, cy, px,
-                                                              py, ox, oy, g_at_one(), base, frac);
+                                                              py, ox, oy, g_at_one(), base, frac, plain);
     count_launch();
     return check_launch();
 }

@@ -104,3 +104,27 @@ def test_planner_matches_oracle_random_views(built):
         ref = oracle.plan_view(lam, pitch, n, n, z, cx, cy, ox * p, oy * p, ox, oy)
         for k in ["k_lo_x", "k_hi_x", "k_lo_y", "k_hi_y", "np_x", "np_y"]:
             assert got[k] == ref[k], (it, k)
+
+
+def test_plain_frt_planner_matches_oracle(built):
+    """Plain Fresnel transform views (no stretch): band from the view's own
+    extent, same integers as the oracle's stretch = 0 planner."""
+    rng = np.random.default_rng(2)
+    for it in range(60):
+        n = int(rng.choice([256, 512, 1024]))
+        lam, pitch = 532e-9, float(rng.uniform(0.3e-6, 0.5e-6))
+        z = float(rng.uniform(0.3, 3.0))
+        B = oracle.plan_view(lam, pitch, n, n, z)["width"]
+        p = B / n
+        ox, oy = int(rng.integers(8, n)), int(rng.integers(8, n))
+        cx = float(rng.uniform(-0.5, 0.5)) * (B - ox * p)
+        cy = float(rng.uniform(-0.5, 0.5)) * (B - oy * p)
+        v = nf.View(z=z, center_x=cx, center_y=cy, width=ox * p, height=oy * p, out_nx=ox,
+                    out_ny=oy, mode=nf.MODE_PLAIN_FRT)
+        got = nf.view_plan(lam, pitch, n, n, v)
+        ref = oracle.plan_view(lam, pitch, n, n, z, cx, cy, ox * p, oy * p, ox, oy, stretch=0)
+        for k in ["k_lo_x", "k_hi_x", "k_lo_y", "k_hi_y", "np_x", "np_y"]:
+            assert got[k] == ref[k], (it, k)
+        assert got["on_full_view_lattice"] == 0
+    with pytest.raises(nf.NufdsError):
+        nf.view_plan(532e-9, 0.4e-6, 64, 64, nf.View(z=0.5, mode=7))
