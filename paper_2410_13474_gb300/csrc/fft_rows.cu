@@ -20,6 +20,7 @@
 // come from a __constant__ table, also built in FP64.
 #include <math.h>
 
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -672,6 +673,7 @@ static int plan_host(int L, FftPlan &p, std::vector<float2> &f2, std::vector<dou
     if (L < 64 || (L % 4) || !choose_radices(L, p)) return -3;
     int t = (L / 16 + 31) / 32 * 32;
     p.threads = t < 64 ? 64 : (t > 512 ? 512 : t);
+    p.pad_threads = p.threads;
     p.ncoarse = (L + 63) / 64;
     p.smem_bytes = sizeof(float2) * (size_t)(host_phys(L) + 1 + 64 + p.ncoarse);
     if (p.smem_bytes > 227 * 1024 - 1024) return -3;
@@ -723,9 +725,9 @@ static void set_smem_attrs(size_t bytes);
 
 static int grid_for(const void *fn, const FftPlan &p, int rows);
 
-// Autotuner of the row passes: time the view pass (the heaviest) with each
-// candidate block size on zeroed buffers and keep the fastest (per device and
-// length, once).  The probe gives every resident CTA four rows, so it measures
+// Autotuner of the row passes: time the view pass and the padded pass with
+// each candidate block size on zeroed buffers and keep the fastest of each
+// (per device and length, once).  The probe gives every resident CTA four rows, so it measures
 // the steady state rather than a one-row tail.  Falls back to the default on
 // any failure.
 static void autotune_threads(FftPlan &p) {
@@ -737,7 +739,7 @@ static void autotune_threads(FftPlan &p) {
                                                   p.smem_bytes);
     const long cap = (512L << 20) / (24L * L);  // in + 2x out + scratch under ~512 MB
     const int rows = (int)std::max(1L, std::min(4L * std::max(sms, 1) * std::max(per, 1), cap));
-    int cands[5] = {128, 192, 256, 384, 512}, best_t = p.threads;
+    int cands[5] = {128, 192, 256, 384, 512}, best_t = p.threads, best_pad = p.pad_threads;
     float best = 1e30f;
     float2 *in = nullptr, *out = nullptr, *scr = nullptr, *chirp = nullptr;
     cudaStream_t st = nullptr;
@@ -753,22 +755,35 @@ static void autotune_threads(FftPlan &p) {
         cudaMemsetAsync(in, 0, nin * sizeof(float2), st);
         cudaMemsetAsync(chirp, 0, (size_t)L * sizeof(float2), st);
         const PassArgs a = fft_pass_args(p);
-        for (int t : cands) {
-            if (t < 64 || t > 512) continue;
-            FftPlan q = p;
-            q.threads = t;
-            const int grid = grid_for((const void *)k_rows_view<float2>, q, rows);
-            for (int rep = 0; rep < 4; ++rep) {
-                if (rep == 1) cudaEventRecord(e0, st);
-                k_rows_view<float2><<<grid, t, p.smem_bytes, st>>>(a, in, L, chirp, out, 2 * L, rows,
-                                                                   scr, nullptr, nullptr);
-            }
-            cudaEventRecord(e1, st);
-            float ms = 0;
-            if (cudaEventSynchronize(e1) == cudaSuccess &&
-                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
-                best = ms;
-                best_t = t;
+        for (int kind = 0; kind < 2; ++kind) {  // 0: view pass, 1: padded pass
+            best = 1e30f;
+            for (int t : cands) {
+                if (t < 64 || t > 512) continue;
+                FftPlan q = p;
+                q.threads = t;
+                const void *fn = kind == 0 ? (const void *)k_rows_view<float2>
+                                           : (const void *)k_rows_pad2<float2, float2>;
+                const int grid = grid_for(fn, q, rows);
+                for (int rep = 0; rep < 4; ++rep) {
+                    if (rep == 1) cudaEventRecord(e0, st);
+                    if (kind == 0)
+                        k_rows_view<float2><<<grid, t, p.smem_bytes, st>>>(
+                            a, in, L, chirp, out, 2 * L, rows, scr, nullptr, nullptr);
+                    else
+                        k_rows_pad2<float2, float2><<<grid, t, p.smem_bytes, st>>>(
+                            a, in, L, out, 2 * L, rows, nullptr, nullptr);
+                }
+                cudaEventRecord(e1, st);
+                float ms = 0;
+                const bool timed = cudaEventSynchronize(e1) == cudaSuccess &&
+                                   cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                if (getenv("NUFDS_DEBUG"))
+                    fprintf(stderr, "nufds: autotune L=%d %s threads=%d: %.4f ms (%d rows)\n", L,
+                            kind == 0 ? "view" : "pad", t, timed ? ms / 3 : -1.0f, rows);
+                if (timed && ms < best) {
+                    best = ms;
+                    (kind == 0 ? best_t : best_pad) = t;
+                }
             }
         }
     }
@@ -781,6 +796,7 @@ static void autotune_threads(FftPlan &p) {
     cudaFree(chirp);
     cudaFree(scr);
     p.threads = best_t;
+    p.pad_threads = best_pad;
 }
 
 int fft_plan_get(int L, const FftPlan **out) {
@@ -909,10 +925,12 @@ int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, 
                      int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
                      cudaStream_t st) {
     if (rows <= 0) return 0;
-    const int grid = grid_for((const void *)k_rows_pad2<float2, float2>, p, rows);
+    FftPlan q = p;
+    q.threads = p.pad_threads;
+    const int grid = grid_for((const void *)k_rows_pad2<float2, float2>, q, rows);
     const PassArgs a = fft_pass_args(p);
 #define L_(TI, TO)                                                                        \
-    k_rows_pad2<TI, TO><<<grid, p.threads, p.smem_bytes, st>>>(a, (const TI *)in, in_ld,  \
+    k_rows_pad2<TI, TO><<<grid, q.threads, p.smem_bytes, st>>>(a, (const TI *)in, in_ld,  \
                                                               (TO *)out, out_ld, rows,    \
                                                               sc_in, sc_out)
     if (in_prec == PREC_F32 && prec == PREC_F32) L_(float2, float2);
