@@ -338,6 +338,30 @@ def run_ours(args, w):
         vp.close()
         del vout
     line["precision_variants"] = variants
+    # the paper's polynomial surrogate for 2F1 (Section 4): plan initialisation
+    # time (its purpose in the paper), step time, distance from the exact path
+    t0 = time.time()
+    pp = nf.Plan(w.wavelength, w.pitch, n, ny, flags=nf.FLAG_PAPER_POLY_M)
+    torch.cuda.synchronize()
+    pinit = (time.time() - t0) * 1e3
+    pout = pp.output_like(view)
+    pp.load(d_holo)
+    pp.reconstruct(view, pout)
+    torch.cuda.synchronize()
+    ksteps = max(3, args.steps // 4)
+    ev0.record(stream)
+    for _ in range(ksteps):
+        pp.load(d_holo)
+        pp.reconstruct(view, pout)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    pms = ev0.elapsed_time(ev1) / ksteps
+    perr = float(torch.linalg.vector_norm(pout - ref_out) / torch.linalg.vector_norm(ref_out))
+    line["paper_variants"] = {"poly_m": {
+        "init_ms": round(pinit, 1), "init_ms_exact": round(init_ms, 1), "ms_per_step": round(pms, 3),
+        "intensity_rel_l2_vs_exact_path": float("%.3e" % perr), "steps": ksteps}}
+    pp.close()
+    del pout
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     plan.close()

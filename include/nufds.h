@@ -62,6 +62,15 @@ extern "C" {
  * (same stream). */
 #define NUFDS_OUT_INTENSITY_ACCUM_F32 2
 
+/* plan flags */
+/* The paper's own surrogate for Eq. 16 (Section 4, initialisation step 1): 2F1
+ * replaced by a degree-8 polynomial in s = lambda f, least-squares fitted to 51
+ * frequencies uniformly spread over |f| <= 1/(2 pitch) at f_y = 0, applied as
+ * 2F1(..; lambda^2 f_x^2 / a_y^2) ~ P(lambda f_x / a_y) in the pull-back, the
+ * output map (Eq. 17) and the view planner.  A paper-literal variant whose
+ * distance from the exact method is reported; not in nufds_reconstruct_noalloc. */
+#define NUFDS_FLAG_PAPER_POLY_M 1
+
 /* reconstruction method of a view */
 #define NUFDS_MODE_NUFDS 0     /* the NU-FDS method (stretch, FrT, Eq. 17 remap)          */
 #define NUFDS_MODE_PLAIN_FRT 1 /* Eq. 2 alone at z: no stretch, x' = x_o (the paper's Fig.
@@ -76,7 +85,7 @@ typedef struct nufds_params {
     double pitch_m;            /* hologram pixel pitch Delta                            */
     int32_t nx, ny;            /* hologram size; each a multiple of 4, 16 <= n <= 16384 */
     int32_t precision;         /* NUFDS_FP32, NUFDS_FP16_STORE or NUFDS_BF16_STORE      */
-    int32_t reserved;          /* must be 0                                             */
+    int32_t flags;             /* 0, or NUFDS_FLAG_PAPER_POLY_M                         */
     uint64_t hbm_budget_bytes; /* cap on device memory the plan may allocate; 0 = none  */
 } nufds_params;
 

@@ -63,6 +63,8 @@ def lib():
                                          _dp, _dp]
             L.or_reconstruct.restype = _i
             L.or_num_threads.restype = _i
+            L.or_set_paper_poly.argtypes = [_i, _d, _d, _dp]
+            L.or_set_paper_poly.restype = None
             _lib = L
     return _lib
 
@@ -179,6 +181,24 @@ def reconstruct(holo: np.ndarray, wavelength: float, pitch: float, z: float, cx=
     if r:
         raise ValueError("invalid view")
     return field, inten
+
+
+class paper_poly:
+    """Context: inside it, Eq. 16 uses the paper's degree-8 polynomial surrogate
+    for 2F1 fitted to 51 frequencies across the band of (lam, pitch) (Section 4)
+    instead of the exact function.  .coef holds its 9 coefficients (in s = lambda f)."""
+
+    def __init__(self, lam, pitch):
+        self.lam, self.pitch = lam, pitch
+        self.coef = np.zeros(9)
+
+    def __enter__(self):
+        lib().or_set_paper_poly(1, self.lam, self.pitch, _ptr(self.coef))
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_paper_poly(0, 0.0, 0.0, None)
+        return False
 
 
 def num_threads() -> int:

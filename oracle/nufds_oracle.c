@@ -184,14 +184,92 @@ double or_hyp2f1(double w) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's polynomial surrogate for 2F1 (Section 4, initialisation step  */
+/* 1): a degree-8 polynomial fitted to 51 frequencies uniformly spread over  */
+/* the hologram's band.  Reading: samples at f_y = 0, f_x = -1/(2 pitch) ..  */
+/* 1/(2 pitch), variable s = lambda f_x (so w = s^2), least squares; applied */
+/* in Eq. 16 as F(w) ~ P(lambda f_x / a_y).  Off by default.                 */
+/* ------------------------------------------------------------------------ */
+#define OR_POLY_DEG 8
+#define OR_POLY_SAMPLES 51
+static int g_poly = 0;
+static double g_pc[OR_POLY_DEG + 1];
+
+/* least squares by Householder QR of the 51 x 9 Vandermonde system */
+static void poly_fit(const double *x, const double *y, int m, int n, double *c) {
+    double A[OR_POLY_SAMPLES][OR_POLY_DEG + 1], b[OR_POLY_SAMPLES];
+    for (int i = 0; i < m; ++i) {
+        double t = 1.0;
+        for (int j = 0; j < n; ++j, t *= x[i]) A[i][j] = t;
+        b[i] = y[i];
+    }
+    for (int k = 0; k < n; ++k) {
+        double nrm = 0.0;
+        for (int i = k; i < m; ++i) nrm += A[i][k] * A[i][k];
+        nrm = sqrt(nrm);
+        double alpha = A[k][k] > 0 ? -nrm : nrm;
+        double v[OR_POLY_SAMPLES];
+        for (int i = 0; i < m; ++i) v[i] = i < k ? 0.0 : A[i][k];
+        v[k] -= alpha;
+        double vv = 0.0;
+        for (int i = k; i < m; ++i) vv += v[i] * v[i];
+        if (vv == 0.0) continue;
+        for (int j = k; j < n; ++j) {
+            double d = 0.0;
+            for (int i = k; i < m; ++i) d += v[i] * A[i][j];
+            for (int i = k; i < m; ++i) A[i][j] -= 2.0 * d / vv * v[i];
+        }
+        double d = 0.0;
+        for (int i = k; i < m; ++i) d += v[i] * b[i];
+        for (int i = k; i < m; ++i) b[i] -= 2.0 * d / vv * v[i];
+    }
+    for (int j = n - 1; j >= 0; --j) { /* back substitution, R c = Q^T b */
+        double t = b[j];
+        for (int k = j + 1; k < n; ++k) t -= A[j][k] * c[k];
+        c[j] = t / A[j][j];
+    }
+}
+
+/* enable (1) or disable (0) the polynomial for a geometry; coefficients out (9) */
+void or_set_paper_poly(int enable, double lam, double pitch, double *coef_out) {
+    g_poly = 0;
+    if (!enable) return;
+    double x[OR_POLY_SAMPLES], y[OR_POLY_SAMPLES];
+    for (int i = 0; i < OR_POLY_SAMPLES; ++i) {
+        double f = (-0.5 + (double)i / (OR_POLY_SAMPLES - 1)) / pitch;
+        x[i] = lam * f;
+        y[i] = or_hyp2f1(x[i] * x[i]);
+    }
+    poly_fit(x, y, OR_POLY_SAMPLES, OR_POLY_DEG + 1, g_pc);
+    if (coef_out)
+        for (int k = 0; k <= OR_POLY_DEG; ++k) coef_out[k] = g_pc[k];
+    g_poly = 1;
+}
+
+static double poly_val(double s) {
+    double p = g_pc[OR_POLY_DEG];
+    for (int k = OR_POLY_DEG - 1; k >= 0; --k) p = p * s + g_pc[k];
+    return p;
+}
+
+static double poly_der(double s) {
+    double p = OR_POLY_DEG * g_pc[OR_POLY_DEG];
+    for (int k = OR_POLY_DEG - 1; k >= 1; --k) p = p * s + k * g_pc[k];
+    return p;
+}
+
+/* F(w) of Eq. 16, w = s^2 (s carries the frequency's sign): exact or the surrogate */
+static double F_of(double w, double s) { return g_poly ? poly_val(s) : or_hyp2f1(w); }
+
+/* ------------------------------------------------------------------------ */
 /* Magnification and the non-uniform stretch (Eqs. 9, 10, 15, 16).          */
 /* ------------------------------------------------------------------------ */
 
 /* Eq. 16: m_x = (1 - l^2 fy^2)^(-1/4) F(l^2 fx^2 / (1 - l^2 fy^2)); m_y swaps x,y. */
 void or_mag(double lam, double fx, double fy, double *mx, double *my) {
     double ax = 1.0 - lam * lam * fx * fx, ay = 1.0 - lam * lam * fy * fy;
-    *mx = pow(ay, -0.25) * or_hyp2f1(lam * lam * fx * fx / ay);
-    *my = pow(ax, -0.25) * or_hyp2f1(lam * lam * fy * fy / ax);
+    *mx = pow(ay, -0.25) * F_of(lam * lam * fx * fx / ay, g_poly ? lam * fx / sqrt(ay) : 0.0);
+    *my = pow(ax, -0.25) * F_of(lam * lam * fy * fy / ax, g_poly ? lam * fy / sqrt(ax) : 0.0);
 }
 
 /* Eqs. 9-10: f' = (fx m_x, fy m_y). */
@@ -222,6 +300,16 @@ static double hyp2f1_deriv(double w) {
 /* Jacobian of f' = Phi(f) w.r.t. f, dimensionless (u = l fx, v = l fy). */
 static void jacobian(double u, double v, double J[2][2]) {
     double ay = 1.0 - v * v, ax = 1.0 - u * u;
+    if (g_poly) {
+        /* d/du [u ay^(-1/4) P(s)] = ay^(-1/4) (P + s P'), s = u / sqrt(ay);
+         * d/dv [u ay^(-1/4) P(s)] = u v ay^(-5/4) (P / 2 + s P') */
+        double sx = u / sqrt(ay), sy = v / sqrt(ax);
+        J[0][0] = pow(ay, -0.25) * (poly_val(sx) + sx * poly_der(sx));
+        J[1][1] = pow(ax, -0.25) * (poly_val(sy) + sy * poly_der(sy));
+        J[0][1] = u * v * pow(ay, -1.25) * (0.5 * poly_val(sx) + sx * poly_der(sx));
+        J[1][0] = u * v * pow(ax, -1.25) * (0.5 * poly_val(sy) + sy * poly_der(sy));
+        return;
+    }
     double wx = u * u / ay, wy = v * v / ax;
     double r = 1.0 - u * u - v * v;
     /* diagonal: Eq. 15 */
@@ -237,8 +325,8 @@ static void jacobian(double u, double v, double J[2][2]) {
 static void phi_uv(double u, double v, double *up, double *vp) {
     /* Eqs. 9, 10, 16 with u = lambda fx, v = lambda fy */
     double ay = 1.0 - v * v, ax = 1.0 - u * u;
-    *up = u * pow(ay, -0.25) * or_hyp2f1(u * u / ay);
-    *vp = v * pow(ax, -0.25) * or_hyp2f1(v * v / ax);
+    *up = u * pow(ay, -0.25) * F_of(u * u / ay, g_poly ? u / sqrt(ay) : 0.0);
+    *vp = v * pow(ax, -0.25) * F_of(v * v / ax, g_poly ? v / sqrt(ax) : 0.0);
 }
 
 /*

@@ -22,6 +22,7 @@ OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 FP32, FP16_STORE, BF16_STORE = 0, 1, 2
 OUT_INTENSITY, OUT_FIELD, OUT_INTENSITY_ACCUM = 0, 1, 2
 MODE_NUFDS, MODE_PLAIN_FRT = 0, 1
+FLAG_PAPER_POLY_M = 1   # the paper's degree-8 polynomial for 2F1 (Section 4)
 
 # every function include/nufds.h declares
 ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",
@@ -39,7 +40,7 @@ class NufdsError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("wavelength_m", ctypes.c_double), ("pitch_m", ctypes.c_double),
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64)]
+                ("flags", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64)]
 
 
 class _View(ctypes.Structure):
@@ -137,14 +138,15 @@ class View:
                      self.out_nx, self.out_ny, self.kind, self.mode)
 
 
-def _params(wavelength, pitch, nx, ny, precision=FP32, budget=0) -> _Params:
-    return _Params(wavelength, pitch, nx, ny, precision, 0, budget)
+def _params(wavelength, pitch, nx, ny, precision=FP32, budget=0, flags=0) -> _Params:
+    return _Params(wavelength, pitch, nx, ny, precision, flags, budget)
 
 
-def view_plan(wavelength: float, pitch: float, nx: int, ny: int, view: View) -> dict:
+def view_plan(wavelength: float, pitch: float, nx: int, ny: int, view: View,
+              flags: int = 0) -> dict:
     """Host-only planner result for one view (band, FFT sizes N', output grid)."""
     info = _ViewInfo()
-    p = _params(wavelength, pitch, nx, ny)
+    p = _params(wavelength, pitch, nx, ny, flags=flags)
     v = view._c()
     _check(lib().nufds_view_plan(ctypes.byref(p), ctypes.byref(v), ctypes.byref(info)),
            "nufds_view_plan")
@@ -163,10 +165,11 @@ class Plan:
     cached oversampled spectrum of one hologram, on the current CUDA device."""
 
     def __init__(self, wavelength: float, pitch: float, nx: int, ny: int, hologram=None,
-                 stream=None, precision: int = FP32, budget: int = 0):
+                 stream=None, precision: int = FP32, budget: int = 0, flags: int = 0):
         self.wavelength, self.pitch, self.nx, self.ny = wavelength, pitch, nx, ny
+        self.flags = flags
         self._p = ctypes.c_void_p()
-        prm = _params(wavelength, pitch, nx, ny, precision, budget)
+        prm = _params(wavelength, pitch, nx, ny, precision, budget, flags)
         holo = None if hologram is None else self._holo_ptr(hologram)
         _check(lib().nufds_plan_create(ctypes.byref(prm), holo, _stream_handle(stream),
                                        ctypes.byref(self._p)), "nufds_plan_create")
@@ -183,7 +186,7 @@ class Plan:
                "nufds_plan_load")
 
     def view_plan(self, view: View) -> dict:
-        return view_plan(self.wavelength, self.pitch, self.nx, self.ny, view)
+        return view_plan(self.wavelength, self.pitch, self.nx, self.ny, view, self.flags)
 
     def output_like(self, view: View):
         import torch

@@ -49,6 +49,12 @@ int check_launch() {
     return NUFDS_ECUDA;
 }
 
+struct Geom {
+    double lam, pitch;
+    int nx, ny;
+    MapFn mf;  // exact 2F1 or the paper's polynomial surrogate
+};
+
 struct ViewPlan {
     int ox, oy;
     long klo_x, khi_x, klo_y, khi_y, kc_x, kc_y;
@@ -73,6 +79,7 @@ struct nufds_plan {
     int device = 0;
     double lam = 0, pitch = 0;
     int nx = 0, ny = 0;
+    Geom geom;  // geometry and map function (exact or polynomial surrogate)
     uint64_t budget = 0;
     const FftPlan *fx = nullptr, *fy = nullptr;
     // full-view band (z independent in lattice units) and its pull-back table
@@ -153,10 +160,16 @@ static long nice_size(long n) {
 
 // The planner: band = floor/ceil of the Eq. 17 image of all boundary pixel
 // centres in lattice units N pitch f'; N' = nice(max(band, (N pitch)^2/(lambda z))).
-struct Geom {
-    double lam, pitch;
-    int nx, ny;
-};
+
+static Geom make_geom(double lam, double pitch, int nx, int ny, int flags) {
+    Geom g;
+    g.lam = lam;
+    g.pitch = pitch;
+    g.nx = nx;
+    g.ny = ny;
+    if (flags & NUFDS_FLAG_PAPER_POLY_M) map_fit_paper_poly(lam, pitch, &g.mf);
+    return g;
+}
 
 static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
     if (!v || !(v->z_m > 0)) return NUFDS_EINVAL;
@@ -208,7 +221,7 @@ static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
         } else {
             double R0 = sqrt(xo * xo + yo * yo + z * z);
             double up, vp;
-            host_phi(xo / R0, yo / R0, &up, &vp);
+            host_phi(xo / R0, yo / R0, &up, &vp, P->mf);
             kx = P->nx * pitch * up / lam;
             ky = P->ny * pitch * vp / lam;
         }
@@ -277,7 +290,7 @@ static int plan_view_cached(nufds_plan *P, const nufds_view *v, ViewPlan *o) {
             P->vcache.splice(P->vcache.begin(), P->vcache, it);
             return kind_ok(v->out_kind) ? NUFDS_OK : NUFDS_EINVAL;
         }
-    Geom g = {P->lam, P->pitch, P->nx, P->ny};
+    Geom g = P->geom;
     int rc = plan_view_impl(&g, v, o);
     if (rc) return rc;
     P->vcache.emplace_front(key, *o);
@@ -461,7 +474,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
         rm_ld = V.ox;
         if ((rc = stage(P, ST_TABLES, 12.0 * V.ox * V.oy, st, [&] {
                  return launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px,
-                                           V.py, V.ox, V.oy, rmb, rmf, st, V.plain);
+                                           V.py, V.ox, V.oy, rmb, rmf, st, V.plain, P->geom.mf);
              })))
             return rc;
     }
@@ -980,7 +993,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
             }
             if (!rc && !V.lattice)
                 rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px, V.py,
-                                        V.ox, V.oy, g.rmb, g.rmf, st, V.plain);
+                                        V.ox, V.oy, g.rmb, g.rmf, st, V.plain, P->geom.mf);
             if (!rc && prec == NUFDS_FP16_STORE &&
                 cudaMemsetAsync(g.acc, 0, 4 * sizeof(double), st) != cudaSuccess)
                 rc = NUFDS_ECUDA;
@@ -1121,8 +1134,9 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     if (!out) return NUFDS_EINVAL;
     *out = nullptr;
     if (!prm || !(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
-        !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->reserved != 0 || prm->nx <= 0 ||
-        prm->ny <= 0 || prm->nx % 4 || prm->ny % 4)
+        !(prm->wavelength_m < 2.0 * prm->pitch_m) ||
+        (prm->flags & ~NUFDS_FLAG_PAPER_POLY_M) != 0 || prm->nx <= 0 || prm->ny <= 0 ||
+        prm->nx % 4 || prm->ny % 4)
         return NUFDS_EINVAL;
     if (prm->precision != NUFDS_FP32 && prm->precision != NUFDS_FP16_STORE &&
         prm->precision != NUFDS_BF16_STORE)
@@ -1141,6 +1155,7 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     P->ny = prm->ny;
     P->budget = prm->hbm_budget_bytes;
     P->prec = prm->precision;
+    P->geom = make_geom(P->lam, P->pitch, P->nx, P->ny, prm->flags);
     int rc;
     if ((rc = fft_plan_get(P->nx, &P->fx)) || (rc = fft_plan_get(P->ny, &P->fy))) {
         free_plan(P);
@@ -1151,7 +1166,7 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     memset(&fv, 0, sizeof fv);
     fv.z_m = 1.0;
     ViewPlan V;
-    Geom g = {P->lam, P->pitch, P->nx, P->ny};
+    Geom g = P->geom;
     if ((rc = plan_view_impl(&g, &fv, &V))) {
         free_plan(P);
         return rc;
@@ -1181,9 +1196,11 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     // full-view pixel lattice (computed at z = 1, valid at every z)
     const double B1 = full_width(P->lam, P->pitch, 1.0);
     if ((rc = launch_pullback_table(P->lam, P->pitch, P->nx, P->ny, P->pb_kx0, P->pb_nkx,
-                                    P->pb_ky0, P->pb_nky, P->pb_base, P->pb_frac, st)) ||
+                                    P->pb_ky0, P->pb_nky, P->pb_base, P->pb_frac, st,
+                                    P->geom.mf)) ||
         (rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, 1.0, 0.0, 0.0, B1 / P->nx,
-                                 B1 / P->ny, P->nx, P->ny, P->rm_base, P->rm_frac, st))) {
+                                 B1 / P->ny, P->nx, P->ny, P->rm_base, P->rm_frac, st, 0,
+                                 P->geom.mf))) {
         free_plan(P);
         return rc;
     }
@@ -1211,7 +1228,8 @@ int nufds_view_plan(const nufds_params *prm, const nufds_view *v, nufds_view_inf
         !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->nx <= 0 || prm->ny <= 0)
         return NUFDS_EINVAL;
     ViewPlan V;
-    Geom g = {prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny};
+    if (prm->flags & ~NUFDS_FLAG_PAPER_POLY_M) return NUFDS_EINVAL;
+    Geom g = make_geom(prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny, prm->flags);
     int rc = plan_view_impl(&g, v, &V);
     if (rc) return rc;
     memset(info, 0, sizeof *info);
@@ -1371,7 +1389,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
                                          const void *d_holo, void *d_out, void *stream) {
     if (!prm || !v || !d_holo || !d_out) return NUFDS_EINVAL;
     if (!(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
-        !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->reserved != 0 || prm->nx <= 0 ||
+        !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->flags != 0 || prm->nx <= 0 ||
         prm->ny <= 0 || prm->nx % 4 || prm->ny % 4)
         return NUFDS_EINVAL;
     if (prm->precision != NUFDS_FP32) return NUFDS_EUNSUPPORTED;
@@ -1379,7 +1397,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
         !fft_size_ok(prm->ny))
         return NUFDS_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
-    const Geom g = {prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny};
+    const Geom g = make_geom(prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny, 0);
     const int nx = prm->nx, ny = prm->ny;
     ViewPlan F, V;
     nufds_view fv;

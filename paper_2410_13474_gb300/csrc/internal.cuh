@@ -77,7 +77,8 @@ struct FftPlan {
     int radix[kMaxPasses] = {};
     int stride[kMaxPasses] = {};   // s_j = L / (r_1 ... r_j)
     int prefix[kMaxPasses] = {};   // r_1 ... r_{j-1}
-    int threads = 0;
+    int threads = 0;                   // block size of the view passes
+    int pad_threads = 0;               // block size of the padded (spectrum) passes
     int ncoarse = 0;                   // ceil(L / 64)
     double dmax = 0;                   // max_n 1 / psi_hat(n - L/2)
     size_t smem_bytes = 0;
@@ -177,12 +178,24 @@ int launch_transpose(const void *in, long in_ld, void *out, long out_ld, int row
 // FP64 maps and tables (maps.cu)
 // ---------------------------------------------------------------------------
 double host_g(double s);                       // int_0^s (1 - t^2)^(-3/4) dt
-void host_phi(double u, double v, double *up, double *vp);  // stretch of Eqs. 9, 10, 16
+// The function of Eq. 16's 2F1 used by the maps: exact (series of its integral
+// form), or the paper's surrogate (Section 4, initialisation step 1): a
+// degree-8 polynomial P(s), s = lambda f, fitted by least squares to 51
+// frequencies spread uniformly over the band |f| <= 1/(2 pitch) at f_y = 0,
+// used as 2F1(..; w) ~ P(lambda f_x / a_y).
+struct MapFn {
+    int poly = 0;
+    double c[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+};
+void map_fit_paper_poly(double lam, double pitch, MapFn *m);
+void host_phi(double u, double v, double *up, double *vp,
+              const MapFn &m = MapFn());  // stretch of Eqs. 9, 10, 16
 double g_at_one();
 
 // Pull-back table over lattice [kx0, kx0+nkx) x [ky0, ky0+nky), layout [kx][ky].
 int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
-                          int nky, short2 *base, float2 *frac, cudaStream_t st);
+                          int nky, short2 *base, float2 *frac, cudaStream_t st,
+                          const MapFn &m = MapFn());
 // Output-map table for pixels x_o = cx + (i - ox/2) px etc. at distance z,
 // layout [j][i]; t' in stretched-lattice units, stored as b = floor(2t') and
 // the fraction 2t' - b in 0.32 fixed point (exact to 2^-32 of a fine cell:
@@ -191,7 +204,7 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
 // plain = 1: the identity map x' = x_o of the plain Fresnel transform instead.
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
                        double px, double py, int ox, int oy, short2 *base, uint2 *frac,
-                       cudaStream_t st, int plain = 0);
+                       cudaStream_t st, int plain = 0, const MapFn &m = MapFn());
 // chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L at n = natural index of the
 // slot (digit-reversed order of plan fp), x_n = (n - L/2) window / L
 int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,

@@ -65,17 +65,89 @@ double g_at_one() {
 
 double host_g(double s) { return g_series(s, g_at_one()); }
 
-__host__ __device__ inline void phi_uv(double u, double v, double g1, double *up, double *vp) {
+// Surrogate g(s) = s P(s) and g'(s) = P(s) + s P'(s) (Horner, degree 8)
+__host__ __device__ inline void poly_g(const MapFn &m, double s, double *g, double *gp) {
+    double p = m.c[8], d = 8.0 * m.c[8];
+    for (int k = 7; k >= 0; --k) {
+        p = p * s + m.c[k];
+        if (k >= 1) d = d * s + k * m.c[k];
+    }
+    *g = s * p;
+    *gp = p + s * d;
+}
+
+__host__ __device__ inline void phi_uv(double u, double v, double g1, const MapFn &m, double *up,
+                                       double *vp) {
     double ay = 1.0 - v * v, ax = 1.0 - u * u;
+    if (m.poly) {
+        double gx, gy, d;
+        poly_g(m, u / sqrt(ay), &gx, &d);
+        poly_g(m, v / sqrt(ax), &gy, &d);
+        *up = sqrt(sqrt(ay)) * gx;
+        *vp = sqrt(sqrt(ax)) * gy;
+        return;
+    }
     *up = sqrt(sqrt(ay)) * g_series(u / sqrt(ay), g1);
     *vp = sqrt(sqrt(ax)) * g_series(v / sqrt(ax), g1);
 }
 
-void host_phi(double u, double v, double *up, double *vp) { phi_uv(u, v, g_at_one(), up, vp); }
+void host_phi(double u, double v, double *up, double *vp, const MapFn &m) {
+    phi_uv(u, v, g_at_one(), m, up, vp);
+}
 
-// Jacobian d(u', v')/d(u, v) of the stretch (Eq. 15 on the diagonal).
-__device__ inline void jac_uv(double u, double v, double g1, double J[4]) {
-    double ay = 1.0 - v * v, ax = 1.0 - u * u, r = 1.0 - u * u - v * v;
+// Least-squares fit of the surrogate: modified Gram-Schmidt on the augmented
+// 51 x (9 + 1) Vandermonde system [A | b] in s = lambda f, b = 2F1(s^2) =
+// g(s) / s from the series above (1 at s = 0).
+void map_fit_paper_poly(double lam, double pitch, MapFn *m) {
+    const int M = 51, N = 9;
+    double A[51][10];
+    const double g1 = g_at_one();
+    for (int i = 0; i < M; ++i) {
+        const double s = lam * (-0.5 + (double)i / (M - 1)) / pitch;
+        double t = 1.0;
+        for (int j = 0; j < N; ++j, t *= s) A[i][j] = t;
+        A[i][N] = s == 0.0 ? 1.0 : g_series(s, g1) / s;
+    }
+    double R[10][10] = {};
+    for (int j = 0; j <= N; ++j) {
+        for (int k = 0; k < j && k < N; ++k) {  // remove the earlier directions
+            double d = 0.0;
+            for (int i = 0; i < M; ++i) d += A[i][k] * A[i][j];
+            R[k][j] = d;
+            for (int i = 0; i < M; ++i) A[i][j] -= d * A[i][k];
+        }
+        if (j < N) {
+            double nrm = 0.0;
+            for (int i = 0; i < M; ++i) nrm += A[i][j] * A[i][j];
+            nrm = sqrt(nrm);
+            R[j][j] = nrm;
+            for (int i = 0; i < M; ++i) A[i][j] /= nrm;
+        }
+    }
+    for (int j = N - 1; j >= 0; --j) {  // R c = Q^T b (column N of R)
+        double t = R[j][N];
+        for (int k = j + 1; k < N; ++k) t -= R[j][k] * m->c[k];
+        m->c[j] = t / R[j][j];
+    }
+    m->poly = 1;
+}
+
+// Jacobian d(u', v')/d(u, v) of the stretch (Eq. 15 on the diagonal).  For the
+// surrogate: du'/du = ay^(-1/4) g'(s), du'/dv = -v/2 ay^(-3/4) g(s) +
+// u v ay^(-5/4) g'(s), s = u / sqrt(ay) (and x <-> y).
+__device__ inline void jac_uv(double u, double v, double g1, const MapFn &m, double J[4]) {
+    double ay = 1.0 - v * v, ax = 1.0 - u * u;
+    if (m.poly) {
+        double gy, dy, gx, dx;
+        poly_g(m, u / sqrt(ay), &gy, &dy);
+        poly_g(m, v / sqrt(ax), &gx, &dx);
+        J[0] = dy / sqrt(sqrt(ay));
+        J[3] = dx / sqrt(sqrt(ax));
+        J[1] = -0.5 * v * gy / sqrt(sqrt(ay * ay * ay)) + u * v * dy / (ay * sqrt(sqrt(ay)));
+        J[2] = -0.5 * u * gx / sqrt(sqrt(ax * ax * ax)) + u * v * dx / (ax * sqrt(sqrt(ax)));
+        return;
+    }
+    double r = 1.0 - u * u - v * v;
     double r34 = 1.0 / sqrt(sqrt(r * r * r));  // r^(-3/4)
     J[0] = sqrt(ay) * r34;
     J[3] = sqrt(ax) * r34;
@@ -86,7 +158,8 @@ __device__ inline void jac_uv(double u, double v, double g1, double J[4]) {
 
 // Inverse of the stretch: solve phi(u, v) = (up, vp) inside the unit disc by
 // damped Newton.  Returns false when (up, vp) has no pre-image.
-__device__ bool pullback_uv(double up, double vp, double g1, double tol, double *uo, double *vo) {
+__device__ bool pullback_uv(double up, double vp, double g1, const MapFn &m, double tol, double *uo,
+                            double *vo) {
     double u = up, v = vp;
     double rr = u * u + v * v;
     if (rr > 0.81) {
@@ -95,11 +168,11 @@ __device__ bool pullback_uv(double up, double vp, double g1, double tol, double 
         v *= sc;
     }
     double fu, fv;
-    phi_uv(u, v, g1, &fu, &fv);
+    phi_uv(u, v, g1, m, &fu, &fv);
     double res = fabs(fu - up) + fabs(fv - vp);
     for (int it = 0; it < 100; ++it) {
         double J[4];
-        jac_uv(u, v, g1, J);
+        jac_uv(u, v, g1, m, J);
         double det = J[0] * J[3] - J[1] * J[2];
         double ru = up - fu, rv = vp - fv;
         double du = (J[3] * ru - J[1] * rv) / det;
@@ -110,7 +183,7 @@ __device__ bool pullback_uv(double up, double vp, double g1, double tol, double 
             double un = u + step * du, vn = v + step * dv;
             if (un * un + vn * vn < 1.0) {
                 double gu, gv;
-                phi_uv(un, vn, g1, &gu, &gv);
+                phi_uv(un, vn, g1, m, &gu, &gv);
                 double rn = fabs(gu - up) + fabs(gv - vp);
                 if (rn < res || rn == 0.0 || step * (fabs(du) + fabs(dv)) <= tol) {
                     u = un;
@@ -144,7 +217,8 @@ __device__ inline void split_fine(double t2, short *base, float *frac) {
 // fine coordinates 2 t with t = N pitch f (centred grid units).  Masked where
 // there is no pre-image or |t_x| > N_x/2 or |t_y| > N_y/2.
 __global__ void k_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx,
-                                 long ky0, int nky, double g1, short2 *base, float2 *frac) {
+                                 long ky0, int nky, double g1, MapFn m, short2 *base,
+                                 float2 *frac) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)nkx * nky) return;
     int ix = (int)(idx / nky), iy = (int)(idx - (long)ix * nky);
@@ -153,7 +227,7 @@ __global__ void k_pullback_table(double lam, double pitch, int nx, int ny, long 
     double u, v;
     short2 b = make_short2(kMasked, kMasked);
     float2 f = make_float2(0.f, 0.f);
-    if (pullback_uv(up, vp, g1, 1e-13 * lam / pitch, &u, &v)) {
+    if (pullback_uv(up, vp, g1, m, 1e-13 * lam / pitch, &u, &v)) {
         double tx = nx * pitch * u / lam, ty = ny * pitch * v / lam;
         if (fabs(tx) <= 0.5 * nx && fabs(ty) <= 0.5 * ny) {
             split_fine(2.0 * tx, &b.x, &f.x);
@@ -176,7 +250,7 @@ __device__ inline void split_fine_fx(double t2, short *base, unsigned int *frac)
 // f_0 = (x_o, y_o) / (lambda R_0), for view pixels; layout [j][i].
 __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z, double cx,
                               double cy, double px, double py, int ox, int oy, double g1,
-                              short2 *base, uint2 *frac, int plain) {
+                              MapFn m, short2 *base, uint2 *frac, int plain) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)ox * oy) return;
     int j = (int)(idx / ox), i = (int)(idx - (long)j * ox);
@@ -187,7 +261,7 @@ __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z
         vp = yo / z;
     } else {
         double R0 = sqrt(xo * xo + yo * yo + z * z);
-        phi_uv(xo / R0, yo / R0, g1, &up, &vp);
+        phi_uv(xo / R0, yo / R0, g1, m, &up, &vp);
     }
     double tx = nx * pitch * up / lam, ty = ny * pitch * vp / lam;
     short2 b;
@@ -233,22 +307,22 @@ __global__ void k_outchirp_table(double kappa, long b0, int nb, OutChirp *E) {
 }
 
 int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
-                          int nky, short2 *base, float2 *frac, cudaStream_t st) {
+                          int nky, short2 *base, float2 *frac, cudaStream_t st, const MapFn &m) {
     long n = (long)nkx * nky;
     if (n <= 0) return 0;
     k_pullback_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lam, pitch, nx, ny, kx0, nkx,
-                                                                 ky0, nky, g_at_one(), base, frac);
+                                                                 ky0, nky, g_at_one(), m, base, frac);
     count_launch();
     return check_launch();
 }
 
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
                        double px, double py, int ox, int oy, short2 *base, uint2 *frac,
-                       cudaStream_t st, int plain) {
+                       cudaStream_t st, int plain, const MapFn &m) {
     long n = (long)ox * oy;
     if (n <= 0) return 0;
     k_remap_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lam, pitch, nx, ny, z, cx, cy, px,
-                                                              py, ox, oy, g_at_one(), base, frac, plain);
+                                                              py, ox, oy, g_at_one(), m, base, frac, plain);
     count_launch();
     return check_launch();
 }

@@ -329,3 +329,50 @@ def test_partial_view_refocuses_in_focus_points_like_the_full_view():
     plan = oracle.plan_view(lam, pitch, n, n, z, cx, cy, 64 * p, 64 * p, 64, 64)
     assert plan["np_x"] < oracle.plan_view(lam, pitch, n, n, z)["np_x"] or \
         plan["k_hi_x"] - plan["k_lo_x"] < 0.5 * n
+
+
+# --- the paper's polynomial surrogate for 2F1 (Section 4, initialisation step 1) ---
+@pytest.mark.parametrize("lam,pitch,max_err", [(0.64e-6, 0.5e-6, 1e-5), (532e-9, 0.307e-6, 1e-3)])
+def test_paper_polynomial_surrogate_fit(lam, pitch, max_err):
+    """Degree 8, 51 frequencies uniform over |f| <= 1/(2 pitch) at f_y = 0:
+    the oracle's Householder fit equals numpy's least squares on the same
+    samples (an independent solver); the samples are symmetric, so the odd
+    coefficients vanish; and its distance from the exact 2F1 over the band
+    (largest at 120 deg FoV, where 2F1 steepens at the band edge) is stated."""
+    from scipy.special import hyp2f1
+    with oracle.paper_poly(lam, pitch) as pp:
+        c = pp.coef.copy()
+    s = lam * (-0.5 + np.arange(51) / 50.0) / pitch
+    y = hyp2f1(0.5, 0.75, 1.5, s * s)
+    ref = np.linalg.lstsq(np.vander(s, 9, increasing=True), y, rcond=None)[0]
+    assert np.allclose(c, ref, rtol=1e-8, atol=1e-10)
+    assert np.all(np.abs(c[1::2]) < 1e-11)
+    ss = np.linspace(s[0], s[-1], 2001)
+    err = np.abs(np.polynomial.polynomial.polyval(ss, c) - hyp2f1(0.5, 0.75, 1.5, ss * ss))
+    print("max |P - 2F1| over the band: %.3e" % err.max())
+    assert err.max() < max_err
+
+
+def test_paper_polynomial_reproduces_printed_stretch(golden):
+    """The paper computed Fig. 4a with its polynomial: f_x = 0.75 um^-1 still
+    lands at 0.8 um^-1 (8K hologram of 0.64 um, pitch 0.5 um)."""
+    g = golden["frequency_stretch_example"]
+    with oracle.paper_poly(g["wavelength"], 0.5e-6):
+        fpx = oracle.forward(g["wavelength"], g["fx"], 0.0)[0]
+    assert abs(fpx - g["fpx"]) < g["tol"]
+
+
+def test_paper_polynomial_variant_distance_from_exact():
+    """The variant against the exact method on a wide-angle point source
+    (120 deg FoV, z = 0.5 m): same peak pixel; the intensity difference is
+    reported."""
+    lam, pitch, n, z = 532e-9, 0.307e-6, 256, 0.5
+    H, xo, yo, p = _point_hologram(200, 60, n=n, z=z, lam=lam, pitch=pitch)
+    _, I = oracle.reconstruct(H, lam, pitch, z)
+    with oracle.paper_poly(lam, pitch):
+        _, Ip = oracle.reconstruct(H, lam, pitch, z)
+    e = float(np.linalg.norm(Ip - I) / np.linalg.norm(I))
+    print("polynomial m vs exact 2F1: intensity rel_l2 = %.3e, peak ratio %.5f"
+          % (e, Ip.max() / I.max()))
+    assert np.unravel_index(np.argmax(Ip), Ip.shape) == np.unravel_index(np.argmax(I), I.shape)
+    assert e < 0.1
