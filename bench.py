@@ -135,6 +135,23 @@ def _traffic(stage):
     return e.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(values, device=None):
+    """Each timing (ms) maximised over the ranks of the default process group
+    (unchanged when there is none): the job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, ms, world):
+    """Units per second of the whole job: every replica processes its own units."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def cpu_baseline(w, min_seconds=10.0, n=1024):
     """The FP64 oracle as it stands on the host cores: full-view reconstruction
     of an n x n hologram of the workload's geometry (its central crop), repeated
@@ -279,14 +296,11 @@ def run_ours(args, w):
     barrier()
     ms_e2e = ev0.elapsed_time(ev1) / args.steps
 
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)
 
     pix = info["out_nx"] * info["out_ny"]
-    value = world * pix / (ms * 1e-3) / 1e6
-    value_e2e = world * pix / (ms_e2e * 1e-3) / 1e6
+    value = whole_job_rate(pix, ms, world) / 1e6
+    value_e2e = whole_job_rate(pix, ms_e2e, world) / 1e6
 
     dom = max(stats, key=lambda s: s["total_ms"])
     per_launch_bytes = dom["bytes"] / dom["launches"]
