@@ -115,12 +115,15 @@ typedef struct nufds_view_info {
 
 /*
  * Create a plan for one hologram geometry and (optionally) load a hologram.
- * Builds, on the device and once per plan, the FP64-derived tables of the
- * inverse stretch (Eqs. 9, 10, 16) on the full-view band and of the output
- * map (Eq. 17) on the full-view pixel lattice; then, if d_hologram_c64 is not
- * NULL, computes and caches its oversampled spectrum (step two, "FT of the
- * hologram").  Synchronises cuda_stream before returning; the caller may free
- * the hologram afterwards.  *out receives the plan (NULL on error).
+ * Builds, on the device, the FP64-derived tables of the inverse stretch
+ * (Eqs. 9, 10, 16) on the full-view band and of the output map (Eq. 17) on
+ * the full-view pixel lattice -- once per (device, wavelength, pitch, size,
+ * flags): plans of the same geometry share them, reference counted, and
+ * nufds_plan_device_bytes counts them in each plan -- then, if
+ * d_hologram_c64 is not NULL, computes and caches its oversampled spectrum
+ * (step two, "FT of the hologram").  Synchronises cuda_stream before
+ * returning; the caller may free the hologram afterwards.  *out receives the
+ * plan (NULL on error).
  */
 int nufds_plan_create(const nufds_params *params, const void *d_hologram_c64,
                       void *cuda_stream, nufds_plan **out);

@@ -14,6 +14,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <list>
 #include <map>
 #include <mutex>
@@ -71,6 +72,8 @@ struct ViewKey {
     bool operator==(const ViewKey &o) const { return memcmp(this, &o, sizeof(ViewKey)) == 0; }
 };
 
+struct GeomTables;
+
 }  // namespace nufds
 
 using namespace nufds;
@@ -90,6 +93,7 @@ struct nufds_plan {
     // output map on the full-view pixel lattice (z independent)
     short2 *rm_base = nullptr;
     uint2 *rm_frac = nullptr;
+    nufds::GeomTables *tab = nullptr;  // owner of the four tables above (shared)
     // cached oversampled spectrum, [mx][my], in the plan's storage precision
     int prec = NUFDS_FP32;
     void *G = nullptr;
@@ -588,12 +592,95 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     return stage(P, ST_REMAP, rm_bytes, st, [&] { return launch_remap(ra, st); });
 }
 
+// The FP64-derived tables of a geometry (pull-back on the full-view band,
+// output map on the full-view pixel lattice) depend only on (device, lambda,
+// pitch, nx, ny, map function): plans of one geometry share them, reference
+// counted (e.g. one resident hologram per precision, or many holograms of
+// one display).
+struct GeomTables {
+    int device, nx, ny, flags;
+    double lam, pitch;
+    short2 *pb_base = nullptr;
+    float2 *pb_frac = nullptr;
+    short2 *rm_base = nullptr;
+    uint2 *rm_frac = nullptr;
+    int refs = 0;
+};
+static std::mutex g_tab_mu;
+static std::vector<GeomTables *> g_tabs;
+
+static void tables_free(GeomTables *t) {
+    cudaFree(t->pb_base);
+    cudaFree(t->pb_frac);
+    cudaFree(t->rm_base);
+    cudaFree(t->rm_frac);
+    delete t;
+}
+
+static void tables_release(GeomTables *t) {
+    if (!t) return;
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (--t->refs > 0) return;
+    for (size_t i = 0; i < g_tabs.size(); ++i)
+        if (g_tabs[i] == t) g_tabs.erase(g_tabs.begin() + (long)i);
+    tables_free(t);
+}
+
+// Find or build (on st, waited for) the tables of P's geometry.
+static int tables_acquire(nufds_plan *P, int flags, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    for (GeomTables *t : g_tabs)
+        if (t->device == P->device && t->lam == P->lam && t->pitch == P->pitch &&
+            t->nx == P->nx && t->ny == P->ny && t->flags == flags) {
+            t->refs++;
+            P->tab = t;
+            return NUFDS_OK;
+        }
+    GeomTables *t = new (std::nothrow) GeomTables();
+    if (!t) return NUFDS_ENOMEM;
+    t->device = P->device;
+    t->lam = P->lam;
+    t->pitch = P->pitch;
+    t->nx = P->nx;
+    t->ny = P->ny;
+    t->flags = flags;
+    const size_t npb = (size_t)P->pb_nkx * P->pb_nky, npix = (size_t)P->nx * P->ny;
+    if (cudaMalloc(&t->pb_base, npb * sizeof(short2)) != cudaSuccess ||
+        cudaMalloc(&t->pb_frac, npb * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&t->rm_base, npix * sizeof(short2)) != cudaSuccess ||
+        cudaMalloc(&t->rm_frac, npix * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        tables_free(t);
+        return NUFDS_ENOMEM;
+    }
+    // inverse stretch on the full-view band; output map on the full-view pixel
+    // lattice (computed at z = 1, valid at every z)
+    const double B1 = full_width(P->lam, P->pitch, 1.0);
+    int rc;
+    if ((rc = launch_pullback_table(P->lam, P->pitch, P->nx, P->ny, P->pb_kx0, P->pb_nkx,
+                                    P->pb_ky0, P->pb_nky, t->pb_base, t->pb_frac, st,
+                                    P->geom.mf)) ||
+        (rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, 1.0, 0.0, 0.0, B1 / P->nx,
+                                 B1 / P->ny, P->nx, P->ny, t->rm_base, t->rm_frac, st, 0,
+                                 P->geom.mf))) {
+        cudaStreamSynchronize(st);
+        tables_free(t);
+        return rc;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        tables_free(t);
+        return NUFDS_ECUDA;
+    }
+    t->refs = 1;
+    g_tabs.push_back(t);
+    P->tab = t;
+    return NUFDS_OK;
+}
+
 static void free_plan(nufds_plan *P) {
     if (!P) return;
-    cudaFree(P->pb_base);
-    cudaFree(P->pb_frac);
-    cudaFree(P->rm_base);
-    cudaFree(P->rm_frac);
+    tables_release(P->tab);
     cudaFree(P->G);
     cudaFree(P->sc);
     cudaFree(P->ws);
@@ -662,8 +749,12 @@ static size_t view_batch_bytes(const BatchView &b, int prec) {
     return t;
 }
 
-// FFT-length classes of the batched row passes (L <= 1024, 2048, .., larger)
-constexpr int kRowClasses = 6;
+// Classes of the batched row passes: FFT length (L <= 1024, 2048, .., larger)
+// x autotuned block size
+constexpr int kLenClasses = 6;
+constexpr int kThreadClasses = 5;
+constexpr int kThreadSizes[kThreadClasses] = {128, 192, 256, 384, 512};
+constexpr int kRowClasses = kLenClasses * kThreadClasses;
 
 static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_t *statuses) {
     // ---- sizes and the workspace
@@ -683,13 +774,19 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         views_bytes += b.bytes;
     }
     const int n = (int)w.size();
-    // Row items of each pass grouped by FFT-length class (L <= 1024, 2048, ..):
-    // one launch per class with that class's shared memory, block size and
-    // grid, so short rows are not run at the occupancy of the longest.
+    // Row items of each pass grouped by FFT-length class (L <= 1024, 2048, ..)
+    // and by the block size the autotuner picked for their length: one launch
+    // per class with that class's shared memory, block size and grid, so short
+    // rows are not run at the occupancy or block size of the longest.
     auto len_class = [](int L) {
         int c = 0;
-        while (c < kRowClasses - 1 && L > (1024 << c)) ++c;
+        while (c < kLenClasses - 1 && L > (1024 << c)) ++c;
         return c;
+    };
+    auto row_class = [&](const FftPlan *f) {
+        int t = 0;
+        while (t < kThreadClasses - 1 && f->threads > kThreadSizes[t]) ++t;
+        return len_class(f->L) * kThreadClasses + t;
     };
     struct RowClass {
         int first = 0, count = 0, rows = 0, threads = 64, maxL = 0, grid = 0;
@@ -703,7 +800,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
             rc.first = (int)order[pass].size();
             for (int i = 0; i < n; ++i) {
                 const FftPlan *f = pass == 0 ? w[i].fpy : w[i].fpx;
-                if (len_class(f->L) != c) continue;
+                if (row_class(f) != c) continue;
                 order[pass].push_back(i);
                 rc.count++;
                 rc.rows += pass == 0 ? w[i].V.npx : 2 * w[i].V.npy;
@@ -1084,6 +1181,25 @@ static int batch_impl(nufds_plan *const *plans, const nufds_view *views, void *c
         }
         all.push_back(b);
     }
+    // views of one plan next to each other (in order of the plan's first
+    // appearance): their stretch gathers then read the same spectrum while it
+    // is in L2, and a wave holds fewer distinct spectra
+    {
+        std::vector<const nufds_plan *> seen;
+        auto rank = [&](const nufds_plan *P) {
+            for (size_t k = 0; k < seen.size(); ++k)
+                if (seen[k] == P) return (int)k;
+            seen.push_back(P);
+            return (int)seen.size() - 1;
+        };
+        std::vector<std::pair<int, int>> key(all.size());
+        for (size_t i = 0; i < all.size(); ++i) key[i] = {rank(all[i].P), (int)i};
+        std::sort(key.begin(), key.end());
+        std::vector<BatchView> sorted;
+        sorted.reserve(all.size());
+        for (auto &k : key) sorted.push_back(all[k.second]);
+        all.swap(sorted);
+    }
     const size_t cap = batch_cap_bytes();
     for (int prec : {NUFDS_FP32, NUFDS_FP16_STORE, NUFDS_BF16_STORE}) {
         std::vector<BatchView> wave;
@@ -1181,29 +1297,21 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
         free_plan(P);
         return NUFDS_ENOMEM;
     }
-    if (cudaMalloc(&P->pb_base, npb * sizeof(short2)) != cudaSuccess ||
-        cudaMalloc(&P->pb_frac, npb * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&P->rm_base, npix * sizeof(short2)) != cudaSuccess ||
-        cudaMalloc(&P->rm_frac, npix * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&P->G, 4 * npix * prec_bytes(P->prec)) != cudaSuccess ||
+    if (cudaMalloc(&P->G, 4 * npix * prec_bytes(P->prec)) != cudaSuccess ||
         cudaMalloc(&P->sc, 256) != cudaSuccess) {
         cudaGetLastError();
         free_plan(P);
         return NUFDS_ENOMEM;
     }
     P->acc = (double *)(P->sc + 16);
-    // FP64 tables: inverse stretch on the full-view band; output map on the
-    // full-view pixel lattice (computed at z = 1, valid at every z)
-    const double B1 = full_width(P->lam, P->pitch, 1.0);
-    if ((rc = launch_pullback_table(P->lam, P->pitch, P->nx, P->ny, P->pb_kx0, P->pb_nkx,
-                                    P->pb_ky0, P->pb_nky, P->pb_base, P->pb_frac, st,
-                                    P->geom.mf)) ||
-        (rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, 1.0, 0.0, 0.0, B1 / P->nx,
-                                 B1 / P->ny, P->nx, P->ny, P->rm_base, P->rm_frac, st, 0,
-                                 P->geom.mf))) {
+    if ((rc = tables_acquire(P, prm->flags, st))) {
         free_plan(P);
         return rc;
     }
+    P->pb_base = P->tab->pb_base;
+    P->pb_frac = P->tab->pb_frac;
+    P->rm_base = P->tab->rm_base;
+    P->rm_frac = P->tab->rm_frac;
     if (d_holo && (rc = load_impl(P, d_holo, st))) {
         free_plan(P);
         return rc;

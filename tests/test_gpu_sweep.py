@@ -89,3 +89,25 @@ def test_sweep_depth_against_oracle(nf):
         print("z = %.2f m: rel_l2 = %.3e" % (DEPTHS[k], e))
         assert e <= 1e-5
     plan.close()
+
+
+def test_plans_of_one_geometry_share_tables(nf):
+    """The FP64 tables are shared by plans of one geometry and map function:
+    results are unchanged when a sibling plan is created or destroyed, and a
+    plan with the polynomial surrogate keeps its own tables."""
+    H = torch.from_numpy(_holo()).cuda()
+    v = nf.View(z=0.7, kind=nf.OUT_FIELD)
+    a = nf.Plan(LAM, PITCH, N, N, H)
+    ref = a.reconstruct(v).clone()
+    b = nf.Plan(LAM, PITCH, N, N, H)
+    poly = nf.Plan(LAM, PITCH, N, N, H, flags=nf.FLAG_PAPER_POLY_M)
+    assert torch.equal(b.reconstruct(v), ref)
+    assert not torch.equal(poly.reconstruct(v), ref)
+    a.close()
+    assert torch.equal(b.reconstruct(v), ref)
+    b.close()
+    c = nf.Plan(LAM, PITCH, N, N, H)
+    assert torch.equal(c.reconstruct(v), ref)
+    torch.cuda.synchronize()
+    c.close()
+    poly.close()
