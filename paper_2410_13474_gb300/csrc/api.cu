@@ -400,7 +400,8 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
     // along y: rows of Bf (2nx rows of ny) -> G (2nx x 2ny)
     if ((rc = stage(P, ST_PAD_ROWS_Y, 48.0 * q * n2, st, [&] {
              return launch_rows_pad2(*P->fy, Bf, P->prec, P->ny, P->G, P->prec, 2 * P->ny,
-                                     2 * P->nx, scale_ptr(P, 0), scale_ptr(P, 1), st);
+                                     2 * P->nx, scale_ptr(P, 0), scale_ptr(P, 1), st,
+                                     1);  // G's columns in natural order (the stretch's reads)
          })))
         return rc;
     P->loaded = true;
@@ -1581,7 +1582,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
                                st)) ||
         (rc = launch_transpose(A, 2 * nx, Bf, ny, ny, 2 * nx, PREC_F32, st)) ||
         (rc = launch_rows_pad2(fy, Bf, PREC_F32, ny, G, PREC_F32, 2 * ny, 2 * nx, nullptr,
-                               nullptr, st)))
+                               nullptr, st, 1)))
         return rc;
     // the view
     if ((rc = launch_chirp_table(fpx, nx * g.pitch, g.lam, V.z, chx, st)) ||

@@ -294,7 +294,7 @@ __device__ __forceinline__ void pad_first_r(const PassArgs &P, const TI *__restr
 }
 
 // pass 0 of the forward DIT: shared -> global, fine index 2k + a = (-1)^k X[k],
-// stored in the plane layout at a L + k
+// stored in the plane layout at a L + k (or at 2k + a when P.natural_out)
 template <int R, class TO>
 __device__ __forceinline__ void dit_last_r(const PassArgs &P, const float2 *sm, const float2 *tws,
                                            TO *__restrict__ orow, float sc, int a) {
@@ -315,7 +315,7 @@ __device__ __forceinline__ void dit_last_r(const PassArgs &P, const float2 *sm, 
             const int f = o + k * s;
             float2 v = x[k];
             if (f & 1) v = make_float2(-v.x, -v.y);
-            st_cs(orow, a * P.L + f, v, sc);
+            st_cs(orow, P.natural_out ? 2 * f + a : a * P.L + f, v, sc);
         }
     }
 }
@@ -923,12 +923,13 @@ int rows_view_grid(const FftPlan &p, int rows) {
 
 int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
                      int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
-                     cudaStream_t st) {
+                     cudaStream_t st, int natural_out) {
     if (rows <= 0) return 0;
     FftPlan q = p;
     q.threads = p.pad_threads;
     const int grid = grid_for((const void *)k_rows_pad2<float2, float2>, q, rows);
-    const PassArgs a = fft_pass_args(p);
+    PassArgs a = fft_pass_args(p);
+    a.natural_out = natural_out;
 #define L_(TI, TO)                                                                        \
     k_rows_pad2<TI, TO><<<grid, q.threads, p.smem_bytes, st>>>(a, (const TI *)in, in_ld,  \
                                                               (TO *)out, out_ld, rows,    \

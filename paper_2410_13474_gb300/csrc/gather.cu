@@ -13,7 +13,10 @@
 // Both read a coordinate table (integer fine-grid base + FP32 fraction,
 // derived in FP64) and wrap indices periodically (the DTFT is periodic).
 // The 2x grids are stored plane-wise per axis (fine index m at
-// (m & 1) * L + m / 2), as the row passes write them.
+// (m & 1) * L + m / 2), as the row passes write them, except the columns of
+// the spectrum G, which are in natural order: a warp of the stretch covers 32
+// consecutive band points along y whose windows step by ~1.5 fine columns, so
+// one contiguous run per row touches fewer sectors than two planes do.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -204,6 +207,77 @@ __device__ __forceinline__ float2 window_sum_inside(const T *__restrict__ A, lon
     return acc;
 }
 
+// Eight consecutive elements row[s .. s+7] as four 2-element vector loads
+// from the aligned-down start plus the ninth element when s is odd.
+__device__ __forceinline__ void load_run8(const float2 *__restrict__ row, int s, float2 *v) {
+    const bool odd = s & 1;
+    const float4 *q = reinterpret_cast<const float4 *>(row + (s & ~1));
+    float2 e[9];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 f = __ldg(q + k);
+        e[2 * k] = lo2(f);
+        e[2 * k + 1] = hi2(f);
+    }
+    e[8] = make_float2(0.f, 0.f);
+    if (odd) e[8] = __ldg(row + s + 7);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = odd ? e[k + 1] : e[k];
+}
+template <class H>
+__device__ __forceinline__ void load_run8_16(const H *__restrict__ row, int s, float2 *v) {
+    const bool odd = s & 1;
+    const uint2 *q = reinterpret_cast<const uint2 *>(row + (s & ~1));
+    unsigned int e[9];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint2 f = __ldg(q + k);
+        e[2 * k] = f.x;
+        e[2 * k + 1] = f.y;
+    }
+    e[8] = 0u;
+    if (odd) e[8] = __ldg(reinterpret_cast<const unsigned int *>(row + s + 7));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const unsigned int u = odd ? e[k + 1] : e[k];
+        H h;
+        memcpy(&h, &u, sizeof(h));
+        v[k] = cvt_c(h);
+    }
+}
+__device__ __forceinline__ void load_run8(const __half2 *__restrict__ row, int s, float2 *v) {
+    load_run8_16(row, s, v);
+}
+__device__ __forceinline__ void load_run8(const __nv_bfloat162 *__restrict__ row, int s,
+                                          float2 *v) {
+    load_run8_16(row, s, v);
+}
+
+// As window_sum_inside, for a grid whose columns are in natural order (rows
+// still plane-wise): the kW columns of a row are one run of kW elements.
+template <class T>
+__device__ __forceinline__ float2 window_sum_natcols(const T *__restrict__ A, long ld, int Lr,
+                                                    int r0, int c0, const float *wr,
+                                                    const float *wc) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kW; ++i) {
+        const int r = r0 + i;
+        const T *row = A + (long)((r & 1) * Lr + (r >> 1)) * ld;
+        float2 v[kW];
+        load_run8(row, c0, v);
+        float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kW; ++j) {
+            sum.x = fmaf(wc[j], v[j].x, sum.x);
+            sum.y = fmaf(wc[j], v[j].y, sum.y);
+        }
+        acc.x = fmaf(wr[i], sum.x, acc.x);
+        acc.y = fmaf(wr[i], sum.y, acc.y);
+    }
+    return acc;
+}
+
 template <class T>
 __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int by) {
     const T *G = (const T *)a.G;
@@ -241,11 +315,11 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
         es_weights(f.x, wx);
         es_weights(f.y, wy);
         if (r0 >= 0 && r0 + kW <= Mx && c0 >= 0 && c0 + kW <= My) {
-            acc = window_sum_inside<false>(G, My, a.Nx, a.Ny, r0, c0, wx, wy);
+            acc = window_sum_natcols(G, My, a.Nx, r0, c0, wx, wy);
         } else {  // the window wraps around the periodic grid
             int cols[kW];
 #pragma unroll
-            for (int j = 0; j < kW; ++j) cols[j] = fine_pos(wrap(c0 + j, My), a.Ny);
+            for (int j = 0; j < kW; ++j) cols[j] = wrap(c0 + j, My);
 #pragma unroll
             for (int i = 0; i < kW; ++i) {
                 const long row = (long)fine_pos(wrap(r0 + i, Mx), a.Nx) * My;

@@ -98,6 +98,7 @@ struct PassArgs {
     const float2 *tw;                 // fine[64] | coarse[ncoarse]: W_L^q = coarse[q>>6] fine[q&63]
     const float2 *mod1, *mod1_slot;   // e^{-i pi (n - L/2)/L}: natural / per slot, group-major
     const float *pad_pre;             // (-1)^n / psi_hat(n - L/2), natural order
+    int natural_out;                  // padded output: 0 plane-wise (a L + k), 1 natural (2k + a)
 };
 
 // kernel arguments of plan p
@@ -157,9 +158,10 @@ int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pa
 // the deapodised row.
 // in_prec: storage of in (PREC_F32 for the hologram); out: storage prec.
 // sc_in / sc_out: device pointers to the FP16 scales of in and out (ignored otherwise).
+// natural_out = 1 stores fine index 2k + a at 2k + a (natural order) instead.
 int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
                      int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
-                     cudaStream_t st);
+                     cudaStream_t st, int natural_out = 0);
 
 // View pass: rows of length L: inverse centred DFT (input already carries
 // (-1)^k), multiply by chirp[n] (complex, includes deapodisation and 1/L),
@@ -240,6 +242,7 @@ struct StretchArgs {
     int pb_nkx, pb_nky;
     long klo_x, khi_x, klo_y, khi_y, kc_x, kc_y;
     int npx, npy;
+    // G's fine columns (y) in natural order, rows (x) plane-wise
     void *S;                // output, layout [jx][jy], npx x npy
     int prec;               // storage of G and S
     const float *sc_g, *sc_s;
