@@ -66,7 +66,7 @@ template <bool INV> __device__ __forceinline__ float2 twmul(float2 a, float2 w) 
     return INV ? cmulc(a, w) : cmul(a, w);
 }
 
-constexpr int smallest_prime(int n) {
+__host__ __device__ constexpr int smallest_prime(int n) {
     for (int p = 2; p * p <= n; ++p)
         if (n % p == 0) return p;
     return n;
@@ -125,9 +125,21 @@ template <bool INV> struct Dft<5, INV> {
     }
 };
 // composite R = A * B: X[k1 + A k2] = sum_{n2} W_R^{n2 k1} W_B^{n2 k2} sum_{n1} x[B n1 + n2] W_A^{n1 k1}
+// x W_R^m for the quarter turns (4 m % R == 0): W = (-i)^q, q = 4 m / R (the
+// conjugate for the inverse) -- a swap and sign, no multiply
+template <bool INV> __device__ __forceinline__ float2 rot_quarter(float2 a, int q) {
+    return q == 0 ? a : (q == 2 ? make_float2(-a.x, -a.y) : (q == 1 ? mul_mi<INV>(a) : mul_mi<!INV>(a)));
+}
+
+// Split of a composite radix: 4 x (R/4) where R is a multiple of 4 (more
+// quarter-turn twiddles than 2 x (R/2)), else smallest prime x rest.
+__host__ __device__ constexpr int split_of(int R) {
+    return (R % 4 == 0 && R > 4) ? 4 : smallest_prime(R);
+}
+
 template <int R, bool INV> struct Dft {
     static __device__ __forceinline__ void run(float2 *x) {
-        constexpr int A = smallest_prime(R);
+        constexpr int A = split_of(R);
         constexpr int B = R / A;
         float2 y[R];
 #pragma unroll
@@ -137,8 +149,11 @@ template <int R, bool INV> struct Dft {
             for (int n1 = 0; n1 < A; ++n1) t[n1] = x[B * n1 + n2];
             Dft<A, INV>::run(t);
 #pragma unroll
-            for (int k1 = 0; k1 < A; ++k1)
-                y[k1 * B + n2] = (n2 * k1 == 0) ? t[k1] : twmul<INV>(t[k1], c_tw[TwOff<R>::v + n2 * k1]);
+            for (int k1 = 0; k1 < A; ++k1) {
+                const int m = n2 * k1;  // a constant after unrolling
+                y[k1 * B + n2] = (4 * m) % R == 0 ? rot_quarter<INV>(t[k1], (4 * m / R) & 3)
+                                                  : twmul<INV>(t[k1], c_tw[TwOff<R>::v + m]);
+            }
         }
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) {
