@@ -83,7 +83,8 @@ typedef struct nufds_plan nufds_plan;
 typedef struct nufds_params {
     double wavelength_m;       /* lambda > 0, lambda < 2 pitch (Eq. 1)                  */
     double pitch_m;            /* hologram pixel pitch Delta                            */
-    int32_t nx, ny;            /* hologram size; each a multiple of 4, 16 <= n <= 16384 */
+    int32_t nx, ny;            /* hologram size; multiple of 4, 64 <= n <= 16384 (else
+                                * NUFDS_EUNSUPPORTED)                                    */
     int32_t precision;         /* NUFDS_FP32, NUFDS_FP16_STORE or NUFDS_BF16_STORE      */
     int32_t flags;             /* 0, or NUFDS_FLAG_PAPER_POLY_M                         */
     uint64_t hbm_budget_bytes; /* cap on device memory the plan may allocate; 0 = none  */

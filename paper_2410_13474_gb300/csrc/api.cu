@@ -690,7 +690,7 @@ static void free_plan(nufds_plan *P) {
 }
 
 static bool fft_size_ok(int n) {
-    if (n < 16 || n > 16384 || n % 4) return false;
+    if (n < 64 || n > 16384 || n % 4) return false;  // row FFTs need L >= 64
     int m = n;
     for (int p : {2, 3, 5})
         while (m % p == 0) m /= p;

@@ -128,3 +128,22 @@ def test_plain_frt_planner_matches_oracle(built):
         assert got["on_full_view_lattice"] == 0
     with pytest.raises(nf.NufdsError):
         nf.view_plan(532e-9, 0.4e-6, 64, 64, nf.View(z=0.5, mode=7))
+
+
+def test_planner_limits(built):
+    """Largest supported FFT: N' <= 24576 per axis (one row per CTA in shared
+    memory); a plain-FrT full view of a 16K hologram needs more and is
+    refused; nx must be a positive multiple of 4."""
+    lam, pitch = 532e-9, 0.307e-6
+    ok = nf.view_plan(lam, pitch, 16384, 16384, nf.View(z=0.8))
+    assert ok["np_x"] <= 24576
+    with pytest.raises(nf.NufdsError) as e:
+        nf.view_plan(lam, pitch, 16384, 16384, nf.View(z=0.8, mode=nf.MODE_PLAIN_FRT))
+    assert e.value.code == nf.EUNSUPPORTED
+    with pytest.raises(nf.NufdsError) as e:
+        nf.view_plan(lam, pitch, 64, 64, nf.View(z=0.5, out_nx=70000, out_ny=8))
+    assert e.value.code == nf.EUNSUPPORTED
+    # a one-pixel view plans to the band around that pixel
+    one = nf.view_plan(lam, pitch, 256, 256, nf.View(z=0.5, width=1e-5, height=1e-5, out_nx=1,
+                                                    out_ny=1))
+    assert one["out_nx"] == 1 and one["k_hi_x"] - one["k_lo_x"] <= 2
