@@ -459,24 +459,15 @@ __global__ void __launch_bounds__(512) k_rows_view_batch(const PassArgs *__restr
                                                          int scr_stride) {
     extern __shared__ float2 sm[];
     __shared__ PassArgs sP;
-    __shared__ int s_item;
     float2 *scr = scratch + (long)blockIdx.x * scr_stride;
     const int total = row_off[nitems];
-    int cur = -1;
+    int cur = -1, it = 0;
     const float2 *tws = nullptr;
     float inv = 1.0f, sc = 1.0f;
     for (int g = blockIdx.x; g < total; g += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = nitems - 1;  // last item with row_off <= g
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (row_off[mid] <= g) lo = mid;
-                else hi = mid - 1;
-            }
-            s_item = lo;
-        }
-        __syncthreads();
-        const int it = s_item;
+        // the item of row g: rows only grow, so walk forward from the last one
+        // (every thread alike; no barrier on the critical path)
+        while (it + 1 < nitems && __ldg(row_off + it + 1) <= g) ++it;
         const RowItem &I = items[it];
         if (it != cur) {
             if (threadIdx.x == 0) sP = args[I.args];

@@ -211,6 +211,16 @@ int launch_remap_table(double lam, double pitch, int nx, int ny, double z, doubl
 // slot (digit-reversed order of plan fp), x_n = (n - L/2) window / L
 int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,
                        cudaStream_t st);
+// Batched chirp tables: item i fills its table with blocks [off[i], off[i+1])
+// of a 1-D grid of 256-thread blocks.
+struct ChirpItem {
+    FftPlan fp;
+    double window_m, lam, z;
+    float2 *chirp;
+};
+int launch_chirp_table_batch(const ChirpItem *d_items, const int *d_off, int nitems,
+                             int total_blocks, cudaStream_t st);
+inline int chirp_blocks(int L) { return (L + 255) / 256; }
 // Output chirp e^{i kappa (b + f)^2 / 4} per axis (b fine base, f its
 // fraction), split so that every large argument is reduced exactly:
 //   e  = e^{i kappa b^2 / 4}          (FP64 phase, reduced, stored FP32),

@@ -275,9 +275,9 @@ __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z
 // chirp at the group-major position of each slot:
 // e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) window / L,
 // n the natural index of the slot in the digit-reversed order of the row FFT
-__global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, float2 *chirp) {
+__device__ inline void chirp_entry(const FftPlan &fp, double window, double lam, double z,
+                                   int slot, float2 *chirp) {
     const int L = fp.L;
-    int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= L) return;
     const int n = fft_index_of_slot(fp, slot);
     const double *deapod = fp.deapod;
@@ -288,6 +288,31 @@ __global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, f
     sincos(ph, &s, &c);
     double a = deapod[n] / L;
     chirp[fft_gm_pos(fp, slot)] = make_float2((float)(c * a), (float)(s * a));
+}
+
+__global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, float2 *chirp) {
+    chirp_entry(fp, window, lam, z, blockIdx.x * blockDim.x + threadIdx.x, chirp);
+}
+
+__global__ void k_chirp_table_batch(const ChirpItem *__restrict__ items,
+                                    const int *__restrict__ off, int nitems) {
+    int lo = 0, hi = nitems - 1;  // last item with off <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const ChirpItem &c = items[lo];
+    chirp_entry(c.fp, c.window_m, c.lam, c.z, ((int)blockIdx.x - off[lo]) * blockDim.x + threadIdx.x,
+                c.chirp);
+}
+
+int launch_chirp_table_batch(const ChirpItem *d_items, const int *d_off, int nitems,
+                             int total_blocks, cudaStream_t st) {
+    if (total_blocks <= 0) return 0;
+    k_chirp_table_batch<<<total_blocks, 256, 0, st>>>(d_items, d_off, nitems);
+    count_launch();
+    return check_launch();
 }
 
 __global__ void k_outchirp_table(double kappa, long b0, int nb, OutChirp *E) {
