@@ -242,6 +242,31 @@ int nufds_reconstruct_noalloc(const nufds_params *params, const nufds_view *view
                               const void *d_hologram_c64, void *d_out, void *cuda_stream);
 
 /*
+ * Wavefront error of the object point (xo, yo, zo) reconstructed from its
+ * hologram (Section 2, Figs. 2c and 2f; Section 4, Fig. 5), in waves, along
+ * the hologram's central row: the phase of the point's spectrum (stationary
+ * phase of e^{-ikR_o} at the local frequency of Eq. 4 of each hologram
+ * pixel) minus the paraxial phase that the Fresnel transform focuses, with
+ * its value at the hologram centre removed.
+ *   mode NUFDS_MODE_NUFDS: frequencies stretched by Eqs. 9-10 (the plan's
+ *     map function: exact 2F1, or the polynomial with NUFDS_FLAG_PAPER_POLY_M),
+ *     focus at z_o and x_o' of Eq. 17; z_r is ignored.
+ *   mode NUFDS_MODE_PLAIN_FRT: the plain transform at distance z_r (z_o when
+ *     z_r <= 0, the paper's Fig. 2c; 1/|c_xl(0,0)| of Eq. 5 gives Fig. 2f),
+ *     focused at z_r lambda f_xl(0,0).
+ * Sample j sits at x_j = (j - (samples-1)/2) nx pitch / samples (metres);
+ * x (may be NULL) and w (may be NULL) receive `samples` doubles; w_j is NaN
+ * where the local frequency leaves the band |lambda f| < lambda/(2 pitch) per
+ * axis or is evanescent.  *max_abs = max |w_j| over the others (0 if none).
+ * Host only: uses no GPU and allocates nothing.  Errors: NUFDS_EINVAL for
+ * NULL params or max_abs, samples < 1, zo <= 0, bad geometry (as in
+ * nufds_plan_create) or an unknown mode or flag.
+ */
+int nufds_wavefront_error(const nufds_params *params, double xo, double yo, double zo,
+                          int32_t mode, double z_r, int32_t samples, double *x, double *w,
+                          double *max_abs);
+
+/*
  * Number of kernel launches issued by this library on the calling thread
  * since the last reset (reset = 1 zeroes it after reading).  Lets a caller
  * count the GPU work a call made.

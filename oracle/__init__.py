@@ -52,6 +52,8 @@ def lib():
             L.or_output_map.argtypes = [_d, _d, _d, _d, _dp, _dp]
             L.or_output_map_iterative_inverse.argtypes = [_d, _d, _d, _d, _i, _dp, _dp]
             L.or_ps_tools.argtypes = [_d, _d, _d, _d, _dp, _dp]
+            L.or_wavefront_error.argtypes = [_d, _d, _i, _d, _d, _d, _i, _d, _i, _dp, _dp]
+            L.or_wavefront_error.restype = _d
             L.or_nice.argtypes = [ctypes.c_int64]
             L.or_nice.restype = ctypes.c_int64
             L.or_plan_view_ex.argtypes = [_d, _d, _i, _i, _d, _d, _d, _d, _d, _i, _i, _i, _i64p,
@@ -122,6 +124,18 @@ def output_map_iterative_inverse(lam, z, xop, yop, steps):
 
 def ps_tools(lam, xo, yo, zo):
     return _pair(lib().or_ps_tools, lam, xo, yo, zo)[1:]
+
+
+def wavefront_error(lam, pitch, n, xo, yo, zo, method="nufds", z_r=0.0, samples=1025):
+    """Wavefront error (waves) along the hologram's central row: returns
+    (x, W, max|W|); method "nufds" (Eq. 17 focus at z_o) or "frt" (plain
+    Fresnel transform at z_r, z_o when z_r <= 0)."""
+    x = np.zeros(samples)
+    w = np.zeros(samples)
+    m = {"nufds": 0, "frt": 1}[method]
+    mx = lib().or_wavefront_error(lam, pitch, int(n), xo, yo, zo, m, z_r, int(samples),
+                                  x.ctypes.data_as(_dp), w.ctypes.data_as(_dp))
+    return x, w, mx
 
 
 def nice(n: int) -> int:

@@ -437,6 +437,73 @@ void or_ps_tools(double lam, double xo, double yo, double zo, double *fxl, doubl
     *cxl = -(yo * yo + zo * zo) / (R * R * R);
 }
 
+/*
+ * Wavefront error of one object point along the hologram's central row
+ * (Section 2, Figs. 2c/2f; Section 4, Fig. 5), in waves.
+ *
+ * Reading (the paper gives the idea, not the formula): the error is the
+ * phase of the point's spectrum minus the phase of the paraxial spectrum the
+ * Fresnel transform focuses, taken where the spectrum carries the point.
+ *   - The hologram e^{-ikR_o} has, by stationary phase, the spectrum phase
+ *     psi(f) = -(f . x_o + z_o sqrt(1/lambda^2 - |f|^2)) cycles, sampled at
+ *     the local frequency f(x) of Eq. 4 of each hologram pixel x.
+ *   - The Fresnel transform at distance z_r focuses the paraxial spectrum
+ *     psi_p(q) = -(q . x_r + z_r (1/lambda - lambda |q|^2 / 2)).
+ *   - NU-FDS (method 0) moves f to q = f' of Eqs. 9-10 and focuses at
+ *     z_r = z_o, x_r = x_o' of Eq. 17; the plain Fresnel transform (method 1)
+ *     keeps q = f and focuses at the given z_r, x_r = z_r lambda f_l(0,0)
+ *     (z_r <= 0: z_r = z_o, the paper's wrong-coordinate reconstruction).
+ *   - W(x) = psi(f(x)) - psi_p(q(x)) - [the same at the hologram centre].
+ * x[j] = (j - (ns-1)/2) (n pitch)/ns across the aperture; samples whose local
+ * frequency leaves the band (|f| >= 1/(2 pitch) on an axis) or is evanescent
+ * get W = NaN.  Returns max |W| over the rest (0 when none).
+ */
+static double wfe_psi(double lam, double fx, double fy, double xo, double yo, double zo) {
+    return -(fx * xo + fy * yo + zo * sqrt(1.0 / (lam * lam) - fx * fx - fy * fy));
+}
+
+static double wfe_psi_p(double lam, double qx, double qy, double xr, double yr, double zr) {
+    return -(qx * xr + qy * yr + zr * (1.0 / lam - 0.5 * lam * (qx * qx + qy * qy)));
+}
+
+/* W before the piston is removed, at local frequency (fx, fy) */
+static double wfe_raw(double lam, double fx, double fy, double xo, double yo, double zo, int method,
+                      double zr, double xr, double yr) {
+    double qx = fx, qy = fy;
+    if (method == 0) or_forward(lam, fx, fy, &qx, &qy);
+    return wfe_psi(lam, fx, fy, xo, yo, zo) - wfe_psi_p(lam, qx, qy, xr, yr, zr);
+}
+
+double or_wavefront_error(double lam, double pitch, int n, double xo, double yo, double zo,
+                          int method, double zr, int ns, double *x, double *w) {
+    double R0 = sqrt(xo * xo + yo * yo + zo * zo);
+    double f0x = xo / (lam * R0), f0y = yo / (lam * R0); /* Eq. 4 at the centre */
+    double xr, yr;
+    if (method == 0) {
+        zr = zo;
+        or_output_map(lam, zo, xo, yo, &xr, &yr); /* Eq. 17 */
+    } else {
+        if (zr <= 0.0) zr = zo;
+        xr = zr * lam * f0x;
+        yr = zr * lam * f0y;
+    }
+    double w0 = wfe_raw(lam, f0x, f0y, xo, yo, zo, method, zr, xr, yr);
+    double fb = 0.5 / pitch, mx = 0.0;
+    for (int j = 0; j < ns; ++j) {
+        double xh = (j - 0.5 * (ns - 1)) * (n * pitch) / ns;
+        double R = sqrt((xh - xo) * (xh - xo) + yo * yo + zo * zo);
+        double fx = -(xh - xo) / (lam * R), fy = yo / (lam * R); /* Eq. 4, y = 0 */
+        double v = NAN;
+        if (fabs(fx) < fb && fabs(fy) < fb && lam * lam * (fx * fx + fy * fy) < 1.0) {
+            v = wfe_raw(lam, fx, fy, xo, yo, zo, method, zr, xr, yr) - w0;
+            if (fabs(v) > mx) mx = fabs(v);
+        }
+        if (x) x[j] = xh;
+        if (w) w[j] = v;
+    }
+    return mx;
+}
+
 /* ------------------------------------------------------------------------ */
 /* View planning (Eq. 1, Eq. 17, Section 4 output-grid choice).              */
 /* ------------------------------------------------------------------------ */

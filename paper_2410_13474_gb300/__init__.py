@@ -28,7 +28,7 @@ FLAG_PAPER_POLY_M = 1   # the paper's degree-8 polynomial for 2F1 (Section 4)
 ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",
                  "nufds_reconstruct_batch", "nufds_reconstruct_sweep", "nufds_destroy", "nufds_plan_device_bytes",
                  "nufds_status_string", "nufds_launch_count", "nufds_profile",
-                 "nufds_profile_read", "nufds_reconstruct_noalloc")
+                 "nufds_profile_read", "nufds_reconstruct_noalloc", "nufds_wavefront_error")
 
 
 class NufdsError(RuntimeError):
@@ -100,6 +100,10 @@ def lib():
         L.nufds_profile_read.argtypes = [vp, ctypes.POINTER(_StageStat), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32)]
         L.nufds_launch_count.argtypes = [ctypes.c_int32]
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.nufds_wavefront_error.argtypes = [ctypes.POINTER(_Params), ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.c_int32, dp, dp, dp]
         L.nufds_launch_count.restype = ctypes.c_int64
         _lib = L
     return _lib
@@ -151,6 +155,24 @@ def view_plan(wavelength: float, pitch: float, nx: int, ny: int, view: View,
     _check(lib().nufds_view_plan(ctypes.byref(p), ctypes.byref(v), ctypes.byref(info)),
            "nufds_view_plan")
     return {name: getattr(info, name) for name, _ in _ViewInfo._fields_ if name != "reserved"}
+
+
+def wavefront_error(wavelength: float, pitch: float, n: int, xo: float, yo: float, zo: float,
+                    mode: int = MODE_NUFDS, z_r: float = 0.0, samples: int = 1025,
+                    flags: int = 0):
+    """Wavefront error (waves) of the point (xo, yo, zo) along the hologram's
+    central row, host only: returns (x, W, max|W|) as numpy arrays and a float;
+    W is NaN where the point's local frequency leaves the band."""
+    import numpy as np
+    x = np.zeros(samples)
+    w = np.zeros(samples)
+    mx = ctypes.c_double()
+    p = _params(wavelength, pitch, n, n, flags=flags)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().nufds_wavefront_error(ctypes.byref(p), xo, yo, zo, mode, z_r, samples,
+                                       x.ctypes.data_as(dp), w.ctypes.data_as(dp),
+                                       ctypes.byref(mx)), "nufds_wavefront_error")
+    return x, w, mx.value
 
 
 def _stream_handle(stream):

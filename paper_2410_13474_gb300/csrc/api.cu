@@ -1347,6 +1347,58 @@ int nufds_plan_load(nufds_plan *P, const void *d_holo, void *stream) {
     return load_impl(P, d_holo, (cudaStream_t)stream);
 }
 
+// Wavefront error along the hologram's central row (Sections 2 and 4).  In
+// direction-cosine units (u = lambda f) the point's spectrum has, by
+// stationary phase, the phase -(u x_o + w z_o)/lambda cycles, w = sqrt(1 - |u|^2);
+// the Fresnel transform at z_r focuses -(u' x_r + z_r (1 - |u'|^2 / 2))/lambda,
+// with u' the stretched frequency (NU-FDS) or u itself (plain transform).
+int nufds_wavefront_error(const nufds_params *prm, double xo, double yo, double zo, int32_t mode,
+                          double z_r, int32_t samples, double *x, double *w, double *max_abs) {
+    if (!prm || !max_abs || samples < 1 || !(zo > 0)) return NUFDS_EINVAL;
+    const double lam = prm->wavelength_m, pitch = prm->pitch_m;
+    if (!(lam > 0) || !(pitch > 0) || !(lam < 2.0 * pitch) || prm->nx <= 0 ||
+        (prm->flags & ~NUFDS_FLAG_PAPER_POLY_M))
+        return NUFDS_EINVAL;
+    if (mode != NUFDS_MODE_NUFDS && mode != NUFDS_MODE_PLAIN_FRT) return NUFDS_EINVAL;
+    const Geom g = make_geom(lam, pitch, prm->nx, prm->ny, prm->flags);
+    const double R0 = sqrt(xo * xo + yo * yo + zo * zo);
+    const double u0 = xo / R0, v0 = yo / R0;  // lambda f_l at the hologram centre (Eq. 4)
+    double zf = zo, xf, yf;                   // the focus of the transform
+    if (mode == NUFDS_MODE_NUFDS) {
+        double a, b;
+        host_phi(u0, v0, &a, &b, g.mf);       // Eq. 17: x_o' = z lambda f_0'
+        xf = zo * a;
+        yf = zo * b;
+    } else {
+        if (z_r > 0) zf = z_r;
+        xf = zf * u0;
+        yf = zf * v0;
+    }
+    auto err = [&](double u, double v) {      // cycles, before the piston
+        double up = u, vp = v;
+        if (mode == NUFDS_MODE_NUFDS) host_phi(u, v, &up, &vp, g.mf);
+        const double obj = u * xo + v * yo + zo * sqrt(1.0 - u * u - v * v);
+        const double par = up * xf + vp * yf + zf * (1.0 - 0.5 * (up * up + vp * vp));
+        return (par - obj) / lam;
+    };
+    const double e0 = err(u0, v0), ub = 0.5 * lam / pitch, aperture = prm->nx * pitch;
+    double mx = 0;
+    for (int j = 0; j < samples; ++j) {
+        const double xh = aperture * (j - 0.5 * (samples - 1)) / samples;
+        const double R = sqrt((xh - xo) * (xh - xo) + yo * yo + zo * zo);
+        const double u = (xo - xh) / R, v = yo / R;
+        double e = NAN;
+        if (fabs(u) < ub && fabs(v) < ub && u * u + v * v < 1.0) {
+            e = err(u, v) - e0;
+            mx = fmax(mx, fabs(e));
+        }
+        if (x) x[j] = xh;
+        if (w) w[j] = e;
+    }
+    *max_abs = mx;
+    return NUFDS_OK;
+}
+
 int nufds_view_plan(const nufds_params *prm, const nufds_view *v, nufds_view_info *info) {
     if (!prm || !v || !info) return NUFDS_EINVAL;
     if (!(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
