@@ -259,8 +259,8 @@ int nufds_reconstruct_noalloc(const nufds_params *params, const nufds_view *view
  * where the local frequency leaves the band |lambda f| < lambda/(2 pitch) per
  * axis or is evanescent.  *max_abs = max |w_j| over the others (0 if none).
  * Host only: uses no GPU and allocates nothing.  Errors: NUFDS_EINVAL for
- * NULL params or max_abs, samples < 1, zo <= 0, bad geometry (as in
- * nufds_plan_create) or an unknown mode or flag.
+ * NULL params or max_abs, samples < 1, zo <= 0, wavelength or pitch <= 0,
+ * wavelength >= 2 pitch, nx <= 0 (ny is not used), an unknown mode or flag.
  */
 int nufds_wavefront_error(const nufds_params *params, double xo, double yo, double zo,
                           int32_t mode, double z_r, int32_t samples, double *x, double *w,
