@@ -376,6 +376,25 @@ def run_ours(args, w):
         "intensity_rel_l2_vs_exact_path": float("%.3e" % perr), "steps": ksteps}}
     pp.close()
     del pout
+    # the paper-literal bilinear resampling (Section 4, steps two and five)
+    lp = nf.Plan(w.wavelength, w.pitch, n, ny, flags=nf.FLAG_PAPER_LINEAR)
+    lout = lp.output_like(view)
+    lp.load(d_holo)
+    lp.reconstruct(view, lout)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(ksteps):
+        lp.load(d_holo)
+        lp.reconstruct(view, lout)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    lms = ev0.elapsed_time(ev1) / ksteps
+    lerr = float(torch.linalg.vector_norm(lout - ref_out) / torch.linalg.vector_norm(ref_out))
+    line["paper_variants"]["linear_interp"] = {
+        "ms_per_step": round(lms, 3), "intensity_rel_l2_vs_exact_path": float("%.3e" % lerr),
+        "steps": ksteps}
+    lp.close()
+    del lout
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     plan.close()

@@ -70,6 +70,17 @@ extern "C" {
  * output map (Eq. 17) and the view planner.  A paper-literal variant whose
  * distance from the exact method is reported; not in nufds_reconstruct_noalloc. */
 #define NUFDS_FLAG_PAPER_POLY_M 1
+/* The paper-literal resampling (Section 4, steps two and five name an
+ * interpolation without its kernel; read as linear, separable in x and y):
+ * S(f'_k) by bilinear interpolation of the unpadded centred DFT of the
+ * hologram at the pulled-back frequency, and O(x_o) by bilinear interpolation
+ * of the native Fresnel-transform grid at x'(x_o) of Eq. 17, both periodic
+ * like the DFT, instead of the ideal (band-limited) resampling.  A variant
+ * whose distance from the exact method is reported.  NUFDS_FP32 storage only
+ * (else NUFDS_EUNSUPPORTED from nufds_plan_create); single-view calls and
+ * sweeps only (a batch gives its views NUFDS_EUNSUPPORTED); combines with
+ * NUFDS_FLAG_PAPER_POLY_M; not in nufds_reconstruct_noalloc. */
+#define NUFDS_FLAG_PAPER_LINEAR 2
 
 /* reconstruction method of a view */
 #define NUFDS_MODE_NUFDS 0     /* the NU-FDS method (stretch, FrT, Eq. 17 remap)          */
@@ -86,7 +97,7 @@ typedef struct nufds_params {
     int32_t nx, ny;            /* hologram size; multiple of 4, 64 <= n <= 16384 (else
                                 * NUFDS_EUNSUPPORTED)                                    */
     int32_t precision;         /* NUFDS_FP32, NUFDS_FP16_STORE or NUFDS_BF16_STORE      */
-    int32_t flags;             /* 0, or NUFDS_FLAG_PAPER_POLY_M                         */
+    int32_t flags;             /* 0, or NUFDS_FLAG_PAPER_POLY_M and/or _PAPER_LINEAR   */
     uint64_t hbm_budget_bytes; /* cap on device memory the plan may allocate; 0 = none  */
 } nufds_params;
 
@@ -119,7 +130,7 @@ typedef struct nufds_view_info {
  * Builds, on the device, the FP64-derived tables of the inverse stretch
  * (Eqs. 9, 10, 16) on the full-view band and of the output map (Eq. 17) on
  * the full-view pixel lattice -- once per (device, wavelength, pitch, size,
- * flags): plans of the same geometry share them, reference counted, and
+ * map function, i.e. NUFDS_FLAG_PAPER_POLY_M): plans of the same geometry share them, reference counted, and
  * nufds_plan_device_bytes counts them in each plan -- then, if
  * d_hologram_c64 is not NULL, computes and caches its oversampled spectrum
  * (step two, "FT of the hologram").  Synchronises cuda_stream before
@@ -163,8 +174,9 @@ int nufds_reconstruct(nufds_plan *plan, const nufds_view *view, void *d_out, voi
  * The batch workspace is kept per (device, stream), so batches on different
  * streams may run concurrently (their plans' spectra are only read).
  * statuses (may be NULL) receives one code per view; a failing view does not
- * stop the others.  Returns NUFDS_OK if every view succeeded, else the first
- * error code.
+ * stop the others (views of a plan created with NUFDS_FLAG_PAPER_LINEAR get
+ * NUFDS_EUNSUPPORTED).  Returns NUFDS_OK if every view succeeded, else the
+ * first error code.
  */
 int nufds_reconstruct_batch(nufds_plan *const *plans, const nufds_view *views,
                             void *const *d_outs, int32_t count, void *cuda_stream,

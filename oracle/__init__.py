@@ -52,6 +52,8 @@ def lib():
             L.or_output_map.argtypes = [_d, _d, _d, _d, _dp, _dp]
             L.or_output_map_iterative_inverse.argtypes = [_d, _d, _d, _d, _i, _dp, _dp]
             L.or_ps_tools.argtypes = [_d, _d, _d, _d, _dp, _dp]
+            L.or_lerp2.argtypes = [_dp, _i, _i, _dp, _dp, ctypes.c_int64, _dp]
+            L.or_set_paper_linear.argtypes = [_i]
             L.or_wavefront_error.argtypes = [_d, _d, _i, _d, _d, _d, _i, _d, _i, _dp, _dp]
             L.or_wavefront_error.restype = _d
             L.or_nice.argtypes = [ctypes.c_int64]
@@ -182,6 +184,17 @@ def nufft2(c: np.ndarray, tx, ty) -> np.ndarray:
     return out
 
 
+def lerp2(c: np.ndarray, tx, ty) -> np.ndarray:
+    """Bilinear interpolation of the grid values of the trigonometric polynomial
+    of nufft2 (its centred DFT), periodic: the paper-literal resampling."""
+    c = np.ascontiguousarray(c, np.complex128)
+    tx, ty = _targets(tx, ty)
+    out = np.empty(tx.size, np.complex128)
+    ny, nx = c.shape
+    lib().or_lerp2(_ptr(c), nx, ny, _ptr(tx), _ptr(ty), tx.size, _ptr(out))
+    return out
+
+
 def reconstruct(holo: np.ndarray, wavelength: float, pitch: float, z: float, cx=0.0, cy=0.0,
                 w=0.0, h=0.0, ox=0, oy=0, stretch=True, threads=0):
     """FP64 NU-FDS reconstruction of a complex64 hologram; returns (field, intensity)."""
@@ -212,6 +225,19 @@ class paper_poly:
 
     def __exit__(self, *exc):
         lib().or_set_paper_poly(0, 0.0, 0.0, None)
+        return False
+
+
+class paper_linear:
+    """Context: inside it, steps two and five resample by bilinear interpolation
+    on the unpadded grids (the paper-literal variant) instead of ideally."""
+
+    def __enter__(self):
+        lib().or_set_paper_linear(1)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_paper_linear(0)
         return False
 
 

@@ -10,7 +10,8 @@
  * the Gauss hypergeometric function from its series, a 2-D Newton solve for
  * the inverse of the frequency stretch, and a Gaussian-gridding type-2 NUFFT
  * (oversampling 2, half-width 14 cells, error ~1e-12 relative to sum|c|) to
- * evaluate trigonometric polynomials off the grid.
+ * evaluate trigonometric polynomials off the grid (or, for the paper-literal
+ * variant, bilinear interpolation between their grid values).
  *
  * Paper: Kozacki et al., "Non-uniform Fourier Domain Stretching method for
  * ultra-wide-angle wave propagation".  Each function cites the equation it
@@ -701,6 +702,50 @@ void or_nufft2(const double *c_re_im, int nx, int ny, const double *tx, const do
     free(p.grid);
 }
 
+/*
+ * Paper-literal resampling variant (Section 4, steps two and five name an
+ * interpolation without its kernel; read as linear, separable in x and y):
+ * the trigonometric polynomial F above is taken on its integer grid only --
+ * the centred DFT -- and interpolated bilinearly between the four grid
+ * points around (tx, ty), periodically like the DFT.  Exact at grid points.
+ */
+static int64_t pmod(int64_t a, int64_t m) { return ((a % m) + m) % m; }
+
+void or_lerp2(const double *c_re_im, int nx, int ny, const double *tx, const double *ty,
+              int64_t nt, double *out_re_im) {
+    size_t total = (size_t)nx * ny;
+    cplx *g = (cplx *)malloc(sizeof(cplx) * total);
+    memcpy(g, c_re_im, sizeof(cplx) * total);
+    centred_dft2(g, nx, ny, -1); /* g[ky][kx] = F(kx - nx/2, ky - ny/2) */
+    cplx *out = (cplx *)out_re_im;
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < nt; ++t) {
+        double x0 = floor(tx[t]), y0 = floor(ty[t]);
+        double ax = tx[t] - x0, ay = ty[t] - y0;
+        cplx v[2][2];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                int64_t kx = pmod((int64_t)x0 + b + nx / 2, nx);
+                int64_t ky = pmod((int64_t)y0 + a + ny / 2, ny);
+                v[a][b] = g[(size_t)ky * nx + kx];
+            }
+        out[t] = (1 - ay) * ((1 - ax) * v[0][0] + ax * v[0][1]) +
+                 ay * ((1 - ax) * v[1][0] + ax * v[1][1]);
+    }
+    free(g);
+}
+
+static int g_linear = 0;
+
+/* Select the resampling of steps two and five: 0 ideal (NUFFT), 1 bilinear. */
+void or_set_paper_linear(int enable) { g_linear = enable != 0; }
+
+static void off_grid(const double *c, int nx, int ny, const double *tx, const double *ty,
+                     int64_t nt, double *out) {
+    if (g_linear) or_lerp2(c, nx, ny, tx, ty, nt, out);
+    else or_nufft2(c, nx, ny, tx, ty, nt, out);
+}
+
 /* ------------------------------------------------------------------------ */
 /* The NU-FDS reconstruction (Section 4, Fig. 3: steps 2, 3 and 5).          */
 /* ------------------------------------------------------------------------ */
@@ -765,7 +810,7 @@ int or_reconstruct(double lam, double pitch, int nx, int ny, const float *holo, 
         }
     }
     cplx *S = (cplx *)malloc(sizeof(cplx) * nS);
-    or_nufft2((const double *)H, nx, ny, tx, ty, (int64_t)nS, (double *)S);
+    off_grid((const double *)H, nx, ny, tx, ty, (int64_t)nS, (double *)S);
     for (size_t s = 0; s < nS; ++s)
         if (!keep[s]) S[s] = 0;
     free(H);
@@ -809,7 +854,7 @@ int or_reconstruct(double lam, double pitch, int nx, int ny, const float *holo, 
         }
     }
     cplx *P = (cplx *)malloc(sizeof(cplx) * nO);
-    or_nufft2((const double *)S, npx, npy, ux, uy, (int64_t)nO, (double *)P);
+    off_grid((const double *)S, npx, npy, ux, uy, (int64_t)nO, (double *)P);
     for (size_t o = 0; o < nO; ++o) {
         double ph = OR_PI * (xq[o] * xq[o] + yq[o] * yq[o]) / (lam * z);
         cplx O = (cos(ph) + I * sin(ph)) * P[o];

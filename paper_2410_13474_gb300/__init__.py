@@ -23,6 +23,7 @@ FP32, FP16_STORE, BF16_STORE = 0, 1, 2
 OUT_INTENSITY, OUT_FIELD, OUT_INTENSITY_ACCUM = 0, 1, 2
 MODE_NUFDS, MODE_PLAIN_FRT = 0, 1
 FLAG_PAPER_POLY_M = 1   # the paper's degree-8 polynomial for 2F1 (Section 4)
+FLAG_PAPER_LINEAR = 2   # bilinear resampling on the unpadded grids (Section 4, steps 2 and 5)
 
 # every function include/nufds.h declares
 ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",

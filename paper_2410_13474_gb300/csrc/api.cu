@@ -100,6 +100,10 @@ struct nufds_plan {
     float *sc = nullptr;   // FP16 scales (see launch_scales_load / _view)
     double *acc = nullptr; // energies behind the FP16 scales
     bool loaded = false;
+    // paper-literal linear interpolation (NUFDS_FLAG_PAPER_LINEAR): the
+    // hologram is loaded with (-1)^n alone (lin_pre: nx, then ny floats)
+    bool linear = false;
+    float *lin_pre = nullptr;
     // workspace arena
     char *ws = nullptr;
     size_t ws_bytes = 0;
@@ -164,6 +168,8 @@ static long nice_size(long n) {
 
 // The planner: band = floor/ceil of the Eq. 17 image of all boundary pixel
 // centres in lattice units N pitch f'; N' = nice(max(band, (N pitch)^2/(lambda z))).
+
+constexpr int kKnownFlags = NUFDS_FLAG_PAPER_POLY_M | NUFDS_FLAG_PAPER_LINEAR;
 
 static Geom make_geom(double lam, double pitch, int nx, int ny, int flags) {
     Geom g;
@@ -389,7 +395,7 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
     // along x: rows of H (ny rows of nx) -> A (ny x 2nx)
     if ((rc = stage(P, ST_PAD_ROWS_X, (8.0 + 16.0 * q) * n2, st, [&] {
              return launch_rows_pad2(*P->fx, H, PREC_F32, P->nx, A, P->prec, 2 * P->nx, P->ny,
-                                     nullptr, scale_ptr(P, 0), st);
+                                     nullptr, scale_ptr(P, 0), st, 0, P->lin_pre);
          })))
         return rc;
     // A (ny x 2nx) -> Bf (2nx x ny)
@@ -401,7 +407,8 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
     if ((rc = stage(P, ST_PAD_ROWS_Y, 48.0 * q * n2, st, [&] {
              return launch_rows_pad2(*P->fy, Bf, P->prec, P->ny, P->G, P->prec, 2 * P->ny,
                                      2 * P->nx, scale_ptr(P, 0), scale_ptr(P, 1), st,
-                                     1);  // G's columns in natural order (the stretch's reads)
+                                     1,  // G's columns in natural order (the stretch's reads)
+                                     P->lin_pre ? P->lin_pre + P->nx : nullptr);
          })))
         return rc;
     P->loaded = true;
@@ -485,11 +492,11 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     }
     // chirp tables (FP64 phases), window N pitch, x_n = (n - N'/2) N pitch / N'
     if ((rc = stage(P, ST_TABLES, 16.0 * V.npx, st, [&] {
-             return launch_chirp_table(*fpx, P->nx * P->pitch, P->lam, V.z, chx, st);
+             return launch_chirp_table(*fpx, P->nx * P->pitch, P->lam, V.z, chx, st, P->linear);
          })))
         return rc;
     if ((rc = stage(P, ST_TABLES, 16.0 * V.npy, st, [&] {
-             return launch_chirp_table(*fpy, P->ny * P->pitch, P->lam, V.z, chy, st);
+             return launch_chirp_table(*fpy, P->ny * P->pitch, P->lam, V.z, chy, st, P->linear);
          })))
         return rc;
     const double kx = M_PI * P->lam * V.z / ((P->nx * P->pitch) * (P->nx * P->pitch));
@@ -502,7 +509,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
             return rc;
     }
     // step two: stretch gather -> S_T in Bf (npx x npy)
-    StretchArgs sa;
+    StretchArgs sa = {};
     sa.G = P->G;
     sa.Nx = P->nx;
     sa.Ny = P->ny;
@@ -522,6 +529,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     sa.npy = V.npy;
     sa.S = S;
     sa.plain = V.plain;
+    sa.linear = P->linear;
     sa.prec = P->prec;
     sa.sc_g = scale_ptr(P, 1);
     sa.sc_s = scale_ptr(P, 2);
@@ -564,7 +572,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
          })))
         return rc;
     // step five: remap
-    RemapArgs ra;
+    RemapArgs ra = {};
     ra.Q = A;
     ra.npx = V.npx;
     ra.npy = V.npy;
@@ -587,6 +595,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ra.out = d_out;
     ra.prec = P->prec;
     ra.sc_q = scale_ptr(P, 5);
+    ra.linear = P->linear;
     // Q region the view maps into, its table, the output
     const double rm_bytes = 32.0 * q * nbx * nby + 12.0 * V.ox * V.oy +
                             (v->out_kind == NUFDS_OUT_INTENSITY_F32 ? 4.0 : 8.0) * V.ox * V.oy;
@@ -684,6 +693,7 @@ static void free_plan(nufds_plan *P) {
     tables_release(P->tab);
     cudaFree(P->G);
     cudaFree(P->sc);
+    cudaFree(P->lin_pre);
     cudaFree(P->ws);
     for (cudaEvent_t e : P->events) cudaEventDestroy(e);
     delete P;
@@ -1185,7 +1195,8 @@ static int batch_impl(nufds_plan *const *plans, const nufds_view *views, void *c
         b.P = P;
         b.kind = views[i].out_kind;
         b.out = outs[i];
-        int rc = plan_view_cached(P, &views[i], &b.V);
+        // the linear variant has single-view kernels only
+        int rc = P->linear ? NUFDS_EUNSUPPORTED : plan_view_cached(P, &views[i], &b.V);
         if (!rc && !b.V.plain &&
             (b.V.klo_x < P->pb_kx0 || b.V.khi_x >= P->pb_kx0 + P->pb_nkx ||
              b.V.klo_y < P->pb_ky0 || b.V.khi_y >= P->pb_ky0 + P->pb_nky))
@@ -1268,12 +1279,14 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     *out = nullptr;
     if (!prm || !(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
         !(prm->wavelength_m < 2.0 * prm->pitch_m) ||
-        (prm->flags & ~NUFDS_FLAG_PAPER_POLY_M) != 0 || prm->nx <= 0 || prm->ny <= 0 ||
+        (prm->flags & ~kKnownFlags) != 0 || prm->nx <= 0 || prm->ny <= 0 ||
         prm->nx % 4 || prm->ny % 4)
         return NUFDS_EINVAL;
     if (prm->precision != NUFDS_FP32 && prm->precision != NUFDS_FP16_STORE &&
         prm->precision != NUFDS_BF16_STORE)
         return NUFDS_EINVAL;
+    if ((prm->flags & NUFDS_FLAG_PAPER_LINEAR) && prm->precision != NUFDS_FP32)
+        return NUFDS_EUNSUPPORTED;
     if (!fft_size_ok(prm->nx) || !fft_size_ok(prm->ny)) return NUFDS_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     nufds_plan *P = new (std::nothrow) nufds_plan();
@@ -1289,6 +1302,7 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     P->budget = prm->hbm_budget_bytes;
     P->prec = prm->precision;
     P->geom = make_geom(P->lam, P->pitch, P->nx, P->ny, prm->flags);
+    P->linear = (prm->flags & NUFDS_FLAG_PAPER_LINEAR) != 0;
     int rc;
     if ((rc = fft_plan_get(P->nx, &P->fx)) || (rc = fft_plan_get(P->ny, &P->fy))) {
         free_plan(P);
@@ -1321,7 +1335,20 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
         return NUFDS_ENOMEM;
     }
     P->acc = (double *)(P->sc + 16);
-    if ((rc = tables_acquire(P, prm->flags, st))) {
+    if (P->linear) {
+        std::vector<float> sg(P->nx + P->ny);
+        for (int n = 0; n < P->nx; ++n) sg[n] = (n & 1) ? -1.0f : 1.0f;
+        for (int n = 0; n < P->ny; ++n) sg[P->nx + n] = (n & 1) ? -1.0f : 1.0f;
+        if (cudaMalloc(&P->lin_pre, sizeof(float) * sg.size()) != cudaSuccess ||
+            cudaMemcpy(P->lin_pre, sg.data(), sizeof(float) * sg.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            free_plan(P);
+            return NUFDS_ENOMEM;
+        }
+    }
+    // the tables depend on the map function only
+    if ((rc = tables_acquire(P, prm->flags & NUFDS_FLAG_PAPER_POLY_M, st))) {
         free_plan(P);
         return rc;
     }
@@ -1357,7 +1384,7 @@ int nufds_wavefront_error(const nufds_params *prm, double xo, double yo, double 
     if (!prm || !max_abs || samples < 1 || !(zo > 0)) return NUFDS_EINVAL;
     const double lam = prm->wavelength_m, pitch = prm->pitch_m;
     if (!(lam > 0) || !(pitch > 0) || !(lam < 2.0 * pitch) || prm->nx <= 0 ||
-        (prm->flags & ~NUFDS_FLAG_PAPER_POLY_M))
+        (prm->flags & ~kKnownFlags))
         return NUFDS_EINVAL;
     if (mode != NUFDS_MODE_NUFDS && mode != NUFDS_MODE_PLAIN_FRT) return NUFDS_EINVAL;
     const Geom g = make_geom(lam, pitch, prm->nx, prm->ny, prm->flags);
@@ -1405,7 +1432,7 @@ int nufds_view_plan(const nufds_params *prm, const nufds_view *v, nufds_view_inf
         !(prm->wavelength_m < 2.0 * prm->pitch_m) || prm->nx <= 0 || prm->ny <= 0)
         return NUFDS_EINVAL;
     ViewPlan V;
-    if (prm->flags & ~NUFDS_FLAG_PAPER_POLY_M) return NUFDS_EINVAL;
+    if (prm->flags & ~kKnownFlags) return NUFDS_EINVAL;
     Geom g = make_geom(prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny, prm->flags);
     int rc = plan_view_impl(&g, v, &V);
     if (rc) return rc;
@@ -1662,7 +1689,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
         ((rc = launch_outchirp_table(kx, ex_b0, nbx, Ex, st)) ||
          (rc = launch_outchirp_table(ky, ey_b0, nby, Ey, st))))
         return rc;
-    StretchArgs sa;
+    StretchArgs sa = {};
     sa.G = G;
     sa.Nx = nx;
     sa.Ny = ny;
@@ -1693,7 +1720,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
         (rc = launch_rows_view(fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr, grid_x,
                                PREC_F32, nullptr, nullptr, st)))
         return rc;
-    RemapArgs ra;
+    RemapArgs ra = {};
     ra.Q = A;
     ra.npx = V.npx;
     ra.npy = V.npy;

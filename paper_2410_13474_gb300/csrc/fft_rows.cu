@@ -929,13 +929,14 @@ int rows_view_grid(const FftPlan &p, int rows) {
 
 int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
                      int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
-                     cudaStream_t st, int natural_out) {
+                     cudaStream_t st, int natural_out, const float *pre) {
     if (rows <= 0) return 0;
     FftPlan q = p;
     q.threads = p.pad_threads;
     const int grid = grid_for((const void *)k_rows_pad2<float2, float2>, q, rows);
     PassArgs a = fft_pass_args(p);
     a.natural_out = natural_out;
+    if (pre) a.pad_pre = pre;
 #define L_(TI, TO)                                                                        \
     k_rows_pad2<TI, TO><<<grid, q.threads, p.smem_bytes, st>>>(a, (const TI *)in, in_ld,  \
                                                               (TO *)out, out_ld, rows,    \

@@ -370,6 +370,9 @@ __global__ void __launch_bounds__(256, 4) k_stretch_batch(const StretchArgs *__r
     stretch_body<T>(a, t % tx, t / tx);
 }
 
+__device__ __forceinline__ void remap_store(const RemapArgs &a, long o, float2 acc, short2 b,
+                                            uint2 F);
+
 template <class T>
 __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const T *Q = (const T *)a.Q;
@@ -416,7 +419,13 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
         }
     }
     acc = make_float2(acc.x * qinv, acc.y * qinv);
-    const long o = (long)j * a.ox + i;
+    remap_store(a, (long)j * a.ox + i, acc, b, F);
+}
+
+// O = P at the output pixel o: |O|^2, added |O|^2, or O times the output chirp
+// of the fine position b + F 2^-32
+__device__ __forceinline__ void remap_store(const RemapArgs &a, long o, float2 acc, short2 b,
+                                            uint2 F) {
     if (a.kind == 0) {
         ((float *)a.out)[o] = fmaf(acc.x, acc.x, acc.y * acc.y);
     } else if (a.kind == 2) {  // accumulate |O|^2 (speckle averaging)
@@ -441,6 +450,82 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     }
 }
 
+// ------------------------------------------------------------------------
+// Paper-literal variant (plan flag NUFDS_FLAG_PAPER_LINEAR, FP32 storage):
+// linear interpolation, separable in x and y, on the unpadded grids instead
+// of the ideal resampling above (Section 4 names interpolation in steps two
+// and five without its kernel).  The even fine samples of G are the centred
+// DFT of the hologram when it is loaded without deapodisation, and the even
+// fine samples of Q the native FrT output when the chirp carries none; both
+// are periodic like the DFT.
+// ------------------------------------------------------------------------
+
+// floor(m / 2) for any sign
+__device__ __forceinline__ int floor_half(int m) { return (m - (m & 1)) / 2; }
+
+// bilinear of a periodic coarse grid (C rows x D columns) stored at
+// A[r * ld + c * cs], at coarse position (i + ax, j + ay), i, j centred
+__device__ __forceinline__ float2 lerp2(const float2 *__restrict__ A, long ld, int cs, int C,
+                                        int D, int i, float ax, int j, float ay) {
+    const int r0 = wrap(i + C / 2, C), r1 = wrap(i + 1 + C / 2, C);
+    const int c0 = wrap(j + D / 2, D), c1 = wrap(j + 1 + D / 2, D);
+    const float2 v00 = __ldg(A + r0 * ld + (long)c0 * cs), v01 = __ldg(A + r0 * ld + (long)c1 * cs);
+    const float2 v10 = __ldg(A + r1 * ld + (long)c0 * cs), v11 = __ldg(A + r1 * ld + (long)c1 * cs);
+    const float bx = 1.0f - ax, by = 1.0f - ay;
+    const float2 u0 = make_float2(by * v00.x + ay * v01.x, by * v00.y + ay * v01.y);
+    const float2 u1 = make_float2(by * v10.x + ay * v11.x, by * v10.y + ay * v11.y);
+    return make_float2(bx * u0.x + ax * u1.x, bx * u0.y + ax * u1.y);
+}
+
+// step two: S(f'_k) = bilinear of the unpadded spectrum at the pulled-back f
+__global__ void __launch_bounds__(256) k_stretch_linear(StretchArgs a) {
+    const int jy = blockIdx.x * 32 + threadIdx.x, jx = blockIdx.y * 8 + threadIdx.y;
+    if (jx >= a.npx || jy >= a.npy) return;
+    const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
+    float2 acc = make_float2(0.f, 0.f);
+    bool valid = false;
+    short2 b = make_short2(0, 0);
+    float2 f = make_float2(0.f, 0.f);
+    if (kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
+        if (a.plain) {
+            if (2 * labs(kx) <= a.Nx && 2 * labs(ky) <= a.Ny) {
+                b = make_short2((short)(2 * kx), (short)(2 * ky));
+                valid = true;
+            }
+        } else {
+            const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
+            b = a.pb_base[t];
+            if (b.x != kMasked) {
+                f = a.pb_frac[t];
+                valid = true;
+            }
+        }
+    }
+    if (valid) {
+        // fine position b + f = 2 (coarse position): rows plane-wise (even
+        // fine row 2c is row c), columns natural (even fine column 2c)
+        acc = lerp2((const float2 *)a.G, 2L * a.Ny, 2, a.Nx, a.Ny, floor_half(b.x),
+                    ((b.x & 1) + f.x) * 0.5f, floor_half(b.y), ((b.y & 1) + f.y) * 0.5f);
+        if ((jx + jy) & 1) acc = make_float2(-acc.x, -acc.y);
+    }
+    ((float2 *)a.S)[(long)jx * a.npy + jy] = acc;
+}
+
+// step five: O(x_o) = bilinear of the native FrT output at x'(x_o)
+__global__ void __launch_bounds__(256) k_remap_linear(RemapArgs a) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    if (i >= a.ox || j >= a.oy) return;
+    const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
+    const short2 b = a.rm_base[t];
+    const uint2 F = a.rm_frac[t];
+    const int px = (int)(b.x - 2 * a.kc_x), py = (int)(b.y - 2 * a.kc_y);
+    const float fx = __uint2float_rz(F.x) * 0x1p-32f, fy = __uint2float_rz(F.y) * 0x1p-32f;
+    // Q: rows = y, columns = x, both plane-wise: even fine index 2c at c
+    const float2 acc = lerp2((const float2 *)a.Q, 2L * a.npx, 1, a.npy, a.npx, floor_half(py),
+                             ((py & 1) + fy) * 0.5f, floor_half(px), ((px & 1) + fx) * 0.5f);
+    remap_store(a, (long)j * a.ox + i, acc, b, F);
+}
+
 template <class T>
 __global__ void __launch_bounds__(256, 4) k_remap(RemapArgs a) {
     remap_body<T>(a, blockIdx.x, blockIdx.y);
@@ -458,7 +543,9 @@ __global__ void __launch_bounds__(256, 4) k_remap_batch(const RemapArgs *__restr
 int launch_stretch(const StretchArgs &a, cudaStream_t st) {
     if (es_init()) return -4;
     dim3 grid((a.npy + 31) / 32, (a.npx + 7) / 8);
-    if (a.prec == PREC_F32) k_stretch<float2><<<grid, dim3(32, 8), 0, st>>>(a);
+    if (a.linear && a.prec != PREC_F32) return -3;
+    if (a.linear) k_stretch_linear<<<grid, dim3(32, 8), 0, st>>>(a);
+    else if (a.prec == PREC_F32) k_stretch<float2><<<grid, dim3(32, 8), 0, st>>>(a);
     else if (a.prec == PREC_F16) k_stretch<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
     else k_stretch<__nv_bfloat162><<<grid, dim3(32, 8), 0, st>>>(a);
     count_launch();
@@ -490,7 +577,9 @@ int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, i
 int launch_remap(const RemapArgs &a, cudaStream_t st) {
     if (es_init()) return -4;
     dim3 grid((a.ox + 31) / 32, (a.oy + 7) / 8);
-    if (a.prec == PREC_F32) k_remap<float2><<<grid, dim3(32, 8), 0, st>>>(a);
+    if (a.linear && a.prec != PREC_F32) return -3;
+    if (a.linear) k_remap_linear<<<grid, dim3(32, 8), 0, st>>>(a);
+    else if (a.prec == PREC_F32) k_remap<float2><<<grid, dim3(32, 8), 0, st>>>(a);
     else if (a.prec == PREC_F16) k_remap<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
     else k_remap<__nv_bfloat162><<<grid, dim3(32, 8), 0, st>>>(a);
     count_launch();

@@ -154,14 +154,14 @@ int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pa
 // Padded forward pass: rows of length L (in, row stride in_ld elements) ->
 // rows of length 2L (out, row stride out_ld), fine index 2k + a stored at a L + k:
 //   out[r][a L + k] = (-1)^k sum_n in[r][n] pre[n] e^{-i pi a (n - L/2)/L} e^{-2 pi i n k/L}
-// with pre = pad_pre.  This is the centred DFT on the 2x oversampled grid of
-// the deapodised row.
+// with pre = pad_pre (or the given pre[L], e.g. (-1)^n alone).  This is the
+// centred DFT on the 2x oversampled grid of the deapodised row.
 // in_prec: storage of in (PREC_F32 for the hologram); out: storage prec.
 // sc_in / sc_out: device pointers to the FP16 scales of in and out (ignored otherwise).
 // natural_out = 1 stores fine index 2k + a at 2k + a (natural order) instead.
 int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
                      int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
-                     cudaStream_t st, int natural_out = 0);
+                     cudaStream_t st, int natural_out = 0, const float *pre = nullptr);
 
 // View pass: rows of length L: inverse centred DFT (input already carries
 // (-1)^k), multiply by chirp[n] (complex, includes deapodisation and 1/L),
@@ -207,16 +207,18 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
                        double px, double py, int ox, int oy, short2 *base, uint2 *frac,
                        cudaStream_t st, int plain = 0, const MapFn &m = MapFn());
-// chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L at n = natural index of the
+// chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L (linear: 1 / L) at n = natural index of the
 // slot (digit-reversed order of plan fp), x_n = (n - L/2) window / L
+// linear = 1: without the deapodisation factor (the bilinear output variant)
 int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,
-                       cudaStream_t st);
+                       cudaStream_t st, int linear = 0);
 // Batched chirp tables: item i fills its table with blocks [off[i], off[i+1])
 // of a 1-D grid of 256-thread blocks.
 struct ChirpItem {
     FftPlan fp;
     double window_m, lam, z;
     float2 *chirp;
+    int linear;
 };
 int launch_chirp_table_batch(const ChirpItem *d_items, const int *d_off, int nitems,
                              int total_blocks, cudaStream_t st);
@@ -258,6 +260,8 @@ struct StretchArgs {
     const float *sc_g, *sc_s;
     double *energy;         // if not null: += sum |S|^2 (before storage rounding)
     int plain;              // 1: no stretch, S(f'_k) = DTFT at f = f'_k (plain FrT)
+    int linear;             // 1: bilinear on the unpadded DFT grid (G's even samples of
+                            //    the hologram loaded without deapodisation)
 };
 int launch_stretch(const StretchArgs &a, cudaStream_t st);
 // batched: item i owns blocks [off[i], off[i+1]) of a 1-D grid (32 x 8 tiles)
@@ -280,6 +284,8 @@ struct RemapArgs {
     void *out;
     int prec;               // storage of Q
     const float *sc_q;
+    int linear;             // 1: bilinear on the native FrT grid (Q's even samples,
+                            //    chirp without deapodisation)
 };
 int launch_remap(const RemapArgs &a, cudaStream_t st);
 int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, int total, int prec,

@@ -276,7 +276,7 @@ __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z
 // e^{i pi x_n^2/(lambda z)} deapod[n] / L, x_n = (n - L/2) window / L,
 // n the natural index of the slot in the digit-reversed order of the row FFT
 __device__ inline void chirp_entry(const FftPlan &fp, double window, double lam, double z,
-                                   int slot, float2 *chirp) {
+                                   int linear, int slot, float2 *chirp) {
     const int L = fp.L;
     if (slot >= L) return;
     const int n = fft_index_of_slot(fp, slot);
@@ -286,12 +286,13 @@ __device__ inline void chirp_entry(const FftPlan &fp, double window, double lam,
     ph -= 2.0 * M_PI * rint(ph / (2.0 * M_PI));
     double s, c;
     sincos(ph, &s, &c);
-    double a = deapod[n] / L;
+    double a = (linear ? 1.0 : deapod[n]) / L;
     chirp[fft_gm_pos(fp, slot)] = make_float2((float)(c * a), (float)(s * a));
 }
 
-__global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, float2 *chirp) {
-    chirp_entry(fp, window, lam, z, blockIdx.x * blockDim.x + threadIdx.x, chirp);
+__global__ void k_chirp_table(FftPlan fp, double window, double lam, double z, int linear,
+                              float2 *chirp) {
+    chirp_entry(fp, window, lam, z, linear, blockIdx.x * blockDim.x + threadIdx.x, chirp);
 }
 
 __global__ void k_chirp_table_batch(const ChirpItem *__restrict__ items,
@@ -303,8 +304,8 @@ __global__ void k_chirp_table_batch(const ChirpItem *__restrict__ items,
         else hi = mid - 1;
     }
     const ChirpItem &c = items[lo];
-    chirp_entry(c.fp, c.window_m, c.lam, c.z, ((int)blockIdx.x - off[lo]) * blockDim.x + threadIdx.x,
-                c.chirp);
+    chirp_entry(c.fp, c.window_m, c.lam, c.z, c.linear,
+                ((int)blockIdx.x - off[lo]) * blockDim.x + threadIdx.x, c.chirp);
 }
 
 int launch_chirp_table_batch(const ChirpItem *d_items, const int *d_off, int nitems,
@@ -353,8 +354,8 @@ int launch_remap_table(double lam, double pitch, int nx, int ny, double z, doubl
 }
 
 int launch_chirp_table(const FftPlan &fp, double window_m, double lam, double z, float2 *chirp,
-                       cudaStream_t st) {
-    k_chirp_table<<<(fp.L + 255) / 256, 256, 0, st>>>(fp, window_m, lam, z, chirp);
+                       cudaStream_t st, int linear) {
+    k_chirp_table<<<(fp.L + 255) / 256, 256, 0, st>>>(fp, window_m, lam, z, linear, chirp);
     count_launch();
     return check_launch();
 }

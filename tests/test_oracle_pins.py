@@ -376,3 +376,49 @@ def test_paper_polynomial_variant_distance_from_exact():
           % (e, Ip.max() / I.max()))
     assert np.unravel_index(np.argmax(Ip), Ip.shape) == np.unravel_index(np.argmax(I), I.shape)
     assert e < 0.1
+
+
+# ---------------------------------------------------------------------------
+# Paper-literal linear resampling (Section 4, steps two and five)
+# ---------------------------------------------------------------------------
+
+def test_lerp2_is_the_dft_on_the_grid_and_linear_between():
+    """or_lerp2 at integer positions is the centred DFT (numpy's FFT); between
+    them it reproduces affine grid data exactly, and across the periodic edge
+    it averages the last and the first grid values."""
+    rng = np.random.default_rng(5)
+    ny, nx = 12, 16
+    c = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    grid = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(c)))  # [ky + ny/2][kx + nx/2]
+    kx = rng.integers(-nx // 2, nx // 2, 20)
+    ky = rng.integers(-ny // 2, ny // 2, 20)
+    got = oracle.lerp2(c, kx.astype(float), ky.astype(float))
+    assert np.abs(got - grid[ky + ny // 2, kx + nx // 2]).max() < 1e-10
+    # affine data: grid values a + b kx + d ky -> c by the inverse centred DFT
+    KX, KY = np.meshgrid(np.arange(nx) - nx // 2, np.arange(ny) - ny // 2)
+    g = (0.3 - 1.1j) + (0.7 + 0.2j) * KX - (0.4 - 0.9j) * KY
+    c_aff = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(g)))
+    tx = rng.uniform(-nx // 2, nx // 2 - 1, 50)
+    ty = rng.uniform(-ny // 2, ny // 2 - 1, 50)
+    want = (0.3 - 1.1j) + (0.7 + 0.2j) * tx - (0.4 - 0.9j) * ty
+    assert np.abs(oracle.lerp2(c_aff, tx, ty) - want).max() < 1e-10
+    # periodic edge: halfway between kx = nx/2 - 1 and kx = -nx/2
+    e = oracle.lerp2(c, [nx / 2 - 0.5], [0.0])[0]
+    assert abs(e - 0.5 * (grid[ny // 2, -1] + grid[ny // 2, 0])) < 1e-10
+
+
+def test_paper_linear_variant_refocuses_and_its_distance_from_ideal():
+    """The bilinear variant still focuses a wide-angle point at its own pixel
+    (the maps are the same), with the loss of the linear interpolant; its
+    distance from the ideal method is reported."""
+    lam, pitch, n, z = 532e-9, 0.307e-6, 256, 0.5
+    H, xo, yo, p = _point_hologram(200, 60, n=n, z=z, lam=lam, pitch=pitch)
+    F, I = oracle.reconstruct(H, lam, pitch, z)
+    with oracle.paper_linear():
+        Fl, Il = oracle.reconstruct(H, lam, pitch, z)
+    e = float(np.linalg.norm(Il - I) / np.linalg.norm(I))
+    print("bilinear vs ideal resampling: intensity rel_l2 = %.3e, peak ratio %.4f"
+          % (e, Il.max() / I.max()))
+    assert np.unravel_index(np.argmax(Il), Il.shape) == np.unravel_index(np.argmax(I), I.shape)
+    assert 1e-4 < e < 1.0
+    assert 0.1 < Il.max() / I.max() < 1.0  # a phasor turning ~1.8 rad per bin loses amplitude
