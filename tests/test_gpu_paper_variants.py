@@ -60,25 +60,28 @@ def test_polynomial_variant_vs_oracle(nf, partial):
     exact.close()
 
 
-@pytest.mark.parametrize("geom,partial,poly", [((532e-9, 0.307e-6, 384, 0.6), False, False),
-                                               ((532e-9, 0.4e-6, 256, 0.5), True, False),
-                                               ((640e-9, 0.5e-6, 320, 0.8), False, True)])
+@pytest.mark.parametrize("geom,partial,poly", [((532e-9, 0.307e-6, 384, 384, 0.6), False, False),
+                                               ((532e-9, 0.4e-6, 256, 256, 0.5), True, False),
+                                               ((640e-9, 0.5e-6, 320, 320, 0.8), False, True),
+                                               ((532e-9, 0.4e-6, 320, 192, 0.6), False, False),
+                                               ((532e-9, 0.307e-6, 192, 256, 0.7), True, True)])
 def test_linear_variant_vs_oracle(nf, geom, partial, poly):
     """Paper-literal bilinear resampling (plan flag NUFDS_FLAG_PAPER_LINEAR) on
     the GPU against the oracle running the same variant, field and intensity;
     its distance from the ideal method is the oracle's."""
-    lam, pitch, n, z = geom
+    lam, pitch, nx, ny, z = geom
     pts = synth.points(71, 16, (0.4, 1.2), synth.tan_half_fov(lam, pitch), (0.5, 1.0))
-    H = synth.hologram(pts, lam, pitch, n, n)
+    H = synth.hologram(pts, lam, pitch, nx, ny)
     kw = dict(z=z)
     if partial:
-        B = oracle.plan_view(lam, pitch, n, n, z)["width"]
-        kw = dict(z=z, center_x=-0.2 * B, center_y=0.3 * B, width=0.3 * B, height=0.25 * B,
+        v = oracle.plan_view(lam, pitch, nx, ny, z)
+        B, Bh = v["width"], v["height"]
+        kw = dict(z=z, center_x=-0.2 * B, center_y=0.3 * Bh, width=0.3 * B, height=0.25 * Bh,
                   out_nx=100, out_ny=84)
     flags = nf.FLAG_PAPER_LINEAR | (nf.FLAG_PAPER_POLY_M if poly else 0)
     h = torch.from_numpy(H).cuda()
-    plan = nf.Plan(lam, pitch, n, n, h, flags=flags)
-    ideal = nf.Plan(lam, pitch, n, n, h, flags=nf.FLAG_PAPER_POLY_M if poly else 0)
+    plan = nf.Plan(lam, pitch, nx, ny, h, flags=flags)
+    ideal = nf.Plan(lam, pitch, nx, ny, h, flags=nf.FLAG_PAPER_POLY_M if poly else 0)
     f = plan.reconstruct(nf.View(kind=nf.OUT_FIELD, **kw)).cpu().numpy()
     i = plan.reconstruct(nf.View(**kw)).cpu().numpy()
     fi = ideal.reconstruct(nf.View(kind=nf.OUT_FIELD, **kw)).cpu().numpy()
