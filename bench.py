@@ -152,6 +152,48 @@ def whole_job_rate(units_per_rank, ms, world):
     return world * units_per_rank / (ms * 1e-3)
 
 
+def cufft_comparison(d_holo, info, stages, reps=3):
+    """cuFFT (through torch.fft) timed beside the step's own FFT stages, as a
+    comparison only (it is never part of the product path): the 2x
+    oversampled spectrum of the hologram as one 2N zero-padded 2-D FFT, and the
+    view transforms as an inverse N'_x x N'_y FFT followed by a 2N' zero-padded
+    forward FFT.  Neither includes the chirps, the centring or the gathers
+    that the step's own passes fuse in."""
+    import torch
+    ny, nx = d_holo.shape
+    npx, npy = int(info["np_x"]), int(info["np_y"])
+
+    def timed(fn):
+        r = fn()
+        del r
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+            del r
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    spec_ms = timed(lambda: torch.fft.fft2(d_holo, s=(2 * ny, 2 * nx)))
+    torch.cuda.empty_cache()
+    S = torch.ones((npx, npy), dtype=torch.complex64, device=d_holo.device)
+    view_ms = timed(lambda: torch.fft.fft2(torch.fft.ifft2(S), s=(2 * npx, 2 * npy)))
+    del S
+    torch.cuda.empty_cache()
+
+    def ours(names):
+        return round(sum(stages[k]["ms_per_step"] for k in names if k in stages), 3)
+
+    return {"library": "cuFFT via torch.fft %s" % torch.__version__,
+            "spectrum_2x_padded_ms": round(spec_ms, 3),
+            "ours_spectrum_ms": ours(("pad_rows_x", "pad_transpose", "pad_rows_y")),
+            "view_transforms_ms": round(view_ms, 3),
+            "ours_view_ms": ours(("view_rows_y", "view_transpose", "view_rows_x")),
+            "shapes": {"hologram": [ny, nx], "view": [npx, npy]}}
+
+
 def cpu_baseline(w, min_seconds=10.0, n=1024):
     """The FP64 oracle as it stands on the host cores: full-view reconstruction
     of an n x n hologram of the workload's geometry (its central crop), repeated
@@ -395,6 +437,8 @@ def run_ours(args, w):
         "steps": ksteps}
     lp.close()
     del lout
+    if not args.no_cufft:
+        line["cufft_comparison"] = cufft_comparison(d_holo, info, stages)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     plan.close()
@@ -602,7 +646,7 @@ def run_serve(args):
     served = serve(make(), False)
     single = serve(make(), True)
     sweep = []
-    for mult in (2.0, 5.0):
+    for mult in (2.0, 5.0, 15.0):  # the last beyond one GPU's capacity
         m = min(nreq, max(200, nreq // 5))
         sweep.append({"offered_rate": args.rate * mult, "requests": m,
                       "batched": serve(make(mult, m), False), "one_at_a_time": serve(make(mult, m), True)})
@@ -630,6 +674,8 @@ def main():
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true",
+                    help="skip the cuFFT timed comparison")
     args = ap.parse_args()
     if args.workload == "sweep16k":
         return run_sweep(args)
