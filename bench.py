@@ -438,7 +438,11 @@ def run_ours(args, w):
     lp.close()
     del lout
     if not args.no_cufft:
-        line["cufft_comparison"] = cufft_comparison(d_holo, info, stages)
+        try:
+            line["cufft_comparison"] = cufft_comparison(d_holo, info, stages)
+        except RuntimeError as e:  # e.g. cuFFT out of memory beside the plan
+            torch.cuda.empty_cache()
+            line["cufft_comparison"] = {"error": str(e).splitlines()[0][:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     plan.close()
