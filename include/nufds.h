@@ -254,6 +254,27 @@ int nufds_reconstruct_noalloc(const nufds_params *params, const nufds_view *view
                               const void *d_hologram_c64, void *d_out, void *cuda_stream);
 
 /*
+ * Output coordinate map of Eq. 17 (host only, FP64, the map function the
+ * params' flags select): the FrT output position (xp, yp) at which NU-FDS
+ * reconstructs an object point at (xo, yo) and depth z, all in metres.
+ * NUFDS_EINVAL for bad geometry (as in nufds_wavefront_error), z <= 0 or NULL
+ * outputs.
+ */
+int nufds_output_map(const nufds_params *params, double z, double xo, double yo, double *xp,
+                     double *yp);
+
+/*
+ * The paper's fixed-point iteration for the inverse of Eq. 17 (Section 4, the
+ * second Eq. 18), host only: x_o(1) = x_o', then steps - 1 updates
+ * x_o(k) = x_o' R(k-1) / (z m_x(f_0(k-1))) (and likewise y); the paper uses 4
+ * steps, which reach half a pixel over most of the window (Fig. 4c).  The
+ * library's own remap does not need it (it gathers through Eq. 17 directly).
+ * NUFDS_EINVAL for bad geometry, z <= 0, steps < 1 or NULL outputs.
+ */
+int nufds_output_map_inverse(const nufds_params *params, double z, double xp, double yp,
+                             int32_t steps, double *xo, double *yo);
+
+/*
  * Wavefront error of the object point (xo, yo, zo) reconstructed from its
  * hologram (Section 2, Figs. 2c and 2f; Section 4, Fig. 5), in waves, along
  * the hologram's central row: the phase of the point's spectrum (stationary

@@ -29,7 +29,8 @@ FLAG_PAPER_LINEAR = 2   # bilinear resampling on the unpadded grids (Section 4, 
 ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nufds_reconstruct",
                  "nufds_reconstruct_batch", "nufds_reconstruct_sweep", "nufds_destroy", "nufds_plan_device_bytes",
                  "nufds_status_string", "nufds_launch_count", "nufds_profile",
-                 "nufds_profile_read", "nufds_reconstruct_noalloc", "nufds_wavefront_error")
+                 "nufds_profile_read", "nufds_reconstruct_noalloc", "nufds_wavefront_error",
+                 "nufds_output_map", "nufds_output_map_inverse")
 
 
 class NufdsError(RuntimeError):
@@ -102,6 +103,11 @@ def lib():
                                          ctypes.POINTER(ctypes.c_int32)]
         L.nufds_launch_count.argtypes = [ctypes.c_int32]
         dp = ctypes.POINTER(ctypes.c_double)
+        L.nufds_output_map.argtypes = [ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, dp, dp]
+        L.nufds_output_map_inverse.argtypes = [ctypes.POINTER(_Params), ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                               dp, dp]
         L.nufds_wavefront_error.argtypes = [ctypes.POINTER(_Params), ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                             ctypes.c_double, ctypes.c_int32, dp, dp, dp]
@@ -156,6 +162,26 @@ def view_plan(wavelength: float, pitch: float, nx: int, ny: int, view: View,
     _check(lib().nufds_view_plan(ctypes.byref(p), ctypes.byref(v), ctypes.byref(info)),
            "nufds_view_plan")
     return {name: getattr(info, name) for name, _ in _ViewInfo._fields_ if name != "reserved"}
+
+
+def output_map(wavelength: float, pitch: float, n: int, z: float, xo: float, yo: float,
+               flags: int = 0):
+    """Eq. 17 on the host: (x_o', y_o') for the object point (x_o, y_o) at z."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    p = _params(wavelength, pitch, n, n, flags=flags)
+    _check(lib().nufds_output_map(ctypes.byref(p), z, xo, yo, ctypes.byref(a), ctypes.byref(b)),
+           "nufds_output_map")
+    return a.value, b.value
+
+
+def output_map_inverse(wavelength: float, pitch: float, n: int, z: float, xp: float, yp: float,
+                       steps: int = 4, flags: int = 0):
+    """The paper's fixed-point inverse of Eq. 17 (second Eq. 18), on the host."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    p = _params(wavelength, pitch, n, n, flags=flags)
+    _check(lib().nufds_output_map_inverse(ctypes.byref(p), z, xp, yp, steps, ctypes.byref(a),
+                                          ctypes.byref(b)), "nufds_output_map_inverse")
+    return a.value, b.value
 
 
 def wavefront_error(wavelength: float, pitch: float, n: int, xo: float, yo: float, zo: float,

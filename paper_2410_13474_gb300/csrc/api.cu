@@ -1426,6 +1426,48 @@ int nufds_wavefront_error(const nufds_params *prm, double xo, double yo, double 
     return NUFDS_OK;
 }
 
+static bool host_geom_ok(const nufds_params *prm) {
+    return prm && prm->wavelength_m > 0 && prm->pitch_m > 0 &&
+           prm->wavelength_m < 2.0 * prm->pitch_m && prm->nx > 0 && prm->ny > 0 &&
+           !(prm->flags & ~kKnownFlags);
+}
+
+// Eq. 17: x_o' = z lambda f_0' with f_0 = (x_o, y_o) / (lambda R_0)
+int nufds_output_map(const nufds_params *prm, double z, double xo, double yo, double *xp,
+                     double *yp) {
+    if (!host_geom_ok(prm) || !(z > 0) || !xp || !yp) return NUFDS_EINVAL;
+    const Geom g = make_geom(prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny, prm->flags);
+    const double R = sqrt(xo * xo + yo * yo + z * z);
+    double up, vp;
+    host_phi(xo / R, yo / R, &up, &vp, g.mf);
+    *xp = z * up;
+    *yp = z * vp;
+    return NUFDS_OK;
+}
+
+// The paper's fixed-point iteration for the inverse of Eq. 17 (Section 4,
+// the second Eq. 18): x_o(1) = x_o', x_o(k) = x_o' R(k-1) / (z m_x(f_0(k-1))),
+// m_x = f_0x' / f_0x from the same map function as the plan.
+int nufds_output_map_inverse(const nufds_params *prm, double z, double xp, double yp,
+                             int32_t steps, double *xo, double *yo) {
+    if (!host_geom_ok(prm) || !(z > 0) || steps < 1 || !xo || !yo) return NUFDS_EINVAL;
+    const Geom g = make_geom(prm->wavelength_m, prm->pitch_m, prm->nx, prm->ny, prm->flags);
+    double x = xp, y = yp;
+    for (int k = 2; k <= steps; ++k) {
+        const double R = sqrt(x * x + y * y + z * z), u = x / R, v = y / R;
+        double up, vp;
+        host_phi(u, v, &up, &vp, g.mf);
+        // x' R / (z m_x) with m_x = u' / u, i.e. x' R u / (z u')
+        const double xn = u != 0.0 ? xp * R * u / (z * up) : 0.0;
+        const double yn = v != 0.0 ? yp * R * v / (z * vp) : 0.0;
+        x = xn;
+        y = yn;
+    }
+    *xo = x;
+    *yo = y;
+    return NUFDS_OK;
+}
+
 int nufds_view_plan(const nufds_params *prm, const nufds_view *v, nufds_view_info *info) {
     if (!prm || !v || !info) return NUFDS_EINVAL;
     if (!(prm->wavelength_m > 0) || !(prm->pitch_m > 0) ||
