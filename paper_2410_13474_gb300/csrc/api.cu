@@ -408,7 +408,8 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
              return launch_rows_pad2(*P->fy, Bf, P->prec, P->ny, P->G, P->prec, 2 * P->ny,
                                      2 * P->nx, scale_ptr(P, 0), scale_ptr(P, 1), st,
                                      1,  // G's columns in natural order (the stretch's reads)
-                                     P->lin_pre ? P->lin_pre + P->nx : nullptr);
+                                     P->lin_pre ? P->lin_pre + P->nx : nullptr,
+                                     (float2 *)A, half / sizeof(float2));  // A is free here
          })))
         return rc;
     P->loaded = true;

@@ -310,9 +310,29 @@ __device__ __forceinline__ void pad_first_r(const PassArgs &P, const TI *__restr
 
 // pass 0 of the forward DIT: shared -> global, fine index 2k + a = (-1)^k X[k],
 // stored in the plane layout at a L + k (or at 2k + a when P.natural_out)
+// fine samples 2f and 2f + 1 of a natural-order padded row in one store
+__device__ __forceinline__ void st_pair(float2 *p, long f, float2 e, float2 o, float) {
+    __stcs(reinterpret_cast<float4 *>(p) + f, make_float4(e.x, e.y, o.x, o.y));
+}
+template <class H>
+__device__ __forceinline__ void st_pair_16(H *p, long f, H e, H o) {
+    uint2 u;
+    memcpy(&u.x, &e, sizeof(H));
+    memcpy(&u.y, &o, sizeof(H));
+    __stcs(reinterpret_cast<uint2 *>(p) + f, u);
+}
+__device__ __forceinline__ void st_pair(__half2 *p, long f, float2 e, float2 o, float sc) {
+    st_pair_16(p, f, __float22half2_rn(make_float2(e.x * sc, e.y * sc)),
+               __float22half2_rn(make_float2(o.x * sc, o.y * sc)));
+}
+__device__ __forceinline__ void st_pair(__nv_bfloat162 *p, long f, float2 e, float2 o, float) {
+    st_pair_16(p, f, __float22bfloat162_rn(e), __float22bfloat162_rn(o));
+}
+
 template <int R, class TO>
 __device__ __forceinline__ void dit_last_r(const PassArgs &P, const float2 *sm, const float2 *tws,
-                                           TO *__restrict__ orow, float sc, int a) {
+                                           TO *__restrict__ orow, float sc, int a,
+                                           float2 *__restrict__ pscr) {
     const int s = P.stride[0];
     for (int o = threadIdx.x; o < s; o += blockDim.x) {
         float2 x[R];
@@ -330,7 +350,15 @@ __device__ __forceinline__ void dit_last_r(const PassArgs &P, const float2 *sm, 
             const int f = o + k * s;
             float2 v = x[k];
             if (f & 1) v = make_float2(-v.x, -v.y);
-            st_cs(orow, P.natural_out ? 2 * f + a : a * P.L + f, v, sc);
+            if (P.natural_out == 2) {
+                // paired natural order: the even half waits in this CTA's
+                // scratch row (written and read by the same thread), the odd
+                // half's pass stores fine samples 2f, 2f + 1 together
+                if (a == 0) pscr[f] = v;
+                else st_pair(orow, f, pscr[f], v, sc);
+            } else {
+                st_cs(orow, P.natural_out ? 2 * f + a : a * P.L + f, v, sc);
+            }
         }
     }
 }
@@ -360,12 +388,12 @@ __device__ void mid_pass(const PassArgs &P, int j, float2 *sm, const float2 *tws
 
 template <class TO>
 __device__ void forward_tail(const PassArgs &P, float2 *sm, const float2 *tws, TO *orow, float sc,
-                             int a) {
+                             int a, float2 *pscr = nullptr) {
     for (int j = P.npass - 2; j >= 1; --j) {
         mid_pass<false, true>(P, j, sm, tws);
         __syncthreads();
     }
-#define C_(R) dit_last_r<R, TO>(P, sm, tws, orow, sc, a)
+#define C_(R) dit_last_r<R, TO>(P, sm, tws, orow, sc, a, pscr)
     NUFDS_RADIX_SWITCH(P.radix[0], C_)
 #undef C_
     __syncthreads();
@@ -383,11 +411,12 @@ template <class TI, class TO>
 __global__ void __launch_bounds__(512) k_rows_pad2(PassArgs P, const TI *__restrict__ in,
                                                    long in_ld, TO *__restrict__ out, long out_ld,
                                                    int rows, const float *sc_in,
-                                                   const float *sc_out) {
+                                                   const float *sc_out, float2 *pair_scr) {
     extern __shared__ float2 sm[];
     const float2 *tws = load_tw(P, sm);
     const float inv = sc_in ? 1.0f / *sc_in : 1.0f, sc = sc_out ? *sc_out : 1.0f;
     const int RL = P.radix[P.npass - 1];
+    float2 *pscr = pair_scr ? pair_scr + (long)blockIdx.x * P.L : nullptr;
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         const TI *irow = in + (long)r * in_ld;
         TO *orow = out + (long)r * out_ld;
@@ -396,7 +425,7 @@ __global__ void __launch_bounds__(512) k_rows_pad2(PassArgs P, const TI *__restr
             NUFDS_RADIX_SWITCH(RL, C_)
 #undef C_
             __syncthreads();
-            forward_tail<TO>(P, sm, tws, orow, sc, a);
+            forward_tail<TO>(P, sm, tws, orow, sc, a, pscr);
         }
     }
 }
@@ -777,7 +806,7 @@ static void autotune_threads(FftPlan &p) {
                             a, in, L, chirp, out, 2 * L, rows, scr, nullptr, nullptr);
                     else
                         k_rows_pad2<float2, float2><<<grid, t, p.smem_bytes, st>>>(
-                            a, in, L, out, 2 * L, rows, nullptr, nullptr);
+                            a, in, L, out, 2 * L, rows, nullptr, nullptr, nullptr);
                 }
                 cudaEventRecord(e1, st);
                 float ms = 0;
@@ -929,7 +958,8 @@ int rows_view_grid(const FftPlan &p, int rows) {
 
 int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
                      int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
-                     cudaStream_t st, int natural_out, const float *pre) {
+                     cudaStream_t st, int natural_out, const float *pre, float2 *pair_scr,
+                     size_t pair_cap) {
     if (rows <= 0) return 0;
     FftPlan q = p;
     q.threads = p.pad_threads;
@@ -937,10 +967,12 @@ int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, 
     PassArgs a = fft_pass_args(p);
     a.natural_out = natural_out;
     if (pre) a.pad_pre = pre;
+    if (!natural_out || (size_t)grid * p.L > pair_cap) pair_scr = nullptr;
+    if (pair_scr) a.natural_out = 2;
 #define L_(TI, TO)                                                                        \
     k_rows_pad2<TI, TO><<<grid, q.threads, p.smem_bytes, st>>>(a, (const TI *)in, in_ld,  \
                                                               (TO *)out, out_ld, rows,    \
-                                                              sc_in, sc_out)
+                                                              sc_in, sc_out, pair_scr)
     if (in_prec == PREC_F32 && prec == PREC_F32) L_(float2, float2);
     else if (in_prec == PREC_F32 && prec == PREC_F16) L_(float2, __half2);
     else if (in_prec == PREC_F32 && prec == PREC_BF16) L_(float2, __nv_bfloat162);

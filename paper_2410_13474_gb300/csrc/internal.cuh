@@ -98,7 +98,8 @@ struct PassArgs {
     const float2 *tw;                 // fine[64] | coarse[ncoarse]: W_L^q = coarse[q>>6] fine[q&63]
     const float2 *mod1, *mod1_slot;   // e^{-i pi (n - L/2)/L}: natural / per slot, group-major
     const float *pad_pre;             // (-1)^n / psi_hat(n - L/2), natural order
-    int natural_out;                  // padded output: 0 plane-wise (a L + k), 1 natural (2k + a)
+    int natural_out;                  // padded output: 0 plane-wise (a L + k), 1 natural (2k + a),
+                                      // 2 natural, stored in pairs through a scratch row
 };
 
 // kernel arguments of plan p
@@ -158,10 +159,14 @@ int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pa
 // centred DFT on the 2x oversampled grid of the deapodised row.
 // in_prec: storage of in (PREC_F32 for the hologram); out: storage prec.
 // sc_in / sc_out: device pointers to the FP16 scales of in and out (ignored otherwise).
-// natural_out = 1 stores fine index 2k + a at 2k + a (natural order) instead.
+// natural_out = 1 stores fine index 2k + a at 2k + a (natural order) instead;
+// with pair_scr (device float2 scratch of pair_cap elements, grid x L needed,
+// else ignored) the even half waits there and both halves of a fine pair are
+// stored together (full sectors instead of half-sector writes).
 int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
                      int prec, long out_ld, int rows, const float *sc_in, const float *sc_out,
-                     cudaStream_t st, int natural_out = 0, const float *pre = nullptr);
+                     cudaStream_t st, int natural_out = 0, const float *pre = nullptr,
+                     float2 *pair_scr = nullptr, size_t pair_cap = 0);
 
 // View pass: rows of length L: inverse centred DFT (input already carries
 // (-1)^k), multiply by chirp[n] (complex, includes deapodisation and 1/L),
