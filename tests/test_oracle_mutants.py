@@ -34,6 +34,11 @@ def _build(tmp_path, name, old=None, new=None):
     L.or_centred_dft2.argtypes = [_dp, _i, _i, _i]
     L.or_wavefront_error.argtypes = [_d, _d, _i, _d, _d, _d, _i, _d, _i, _dp, _dp]
     L.or_wavefront_error.restype = _d
+    L.or_nufft2.argtypes = [_dp, _i, _i, _dp, _dp, ctypes.c_int64, _dp]
+    L.or_dtft2_direct.argtypes = [_dp, _i, _i, _dp, _dp, ctypes.c_int64, _dp]
+    L.or_reconstruct.argtypes = [_d, _d, _i, _i, ctypes.POINTER(ctypes.c_float), _d, _d, _d, _d,
+                                 _d, _i, _i, _i, _i, _dp, _dp]
+    L.or_reconstruct.restype = _i
     return L
 
 
@@ -113,6 +118,47 @@ def pin_wavefront_two_ffts(L):
     return bool(np.all(np.isfinite(w[inner]))) and np.abs(w[inner] - w_bf).max() < 0.02
 
 
+def pin_nufft(L):
+    """NUFFT against the direct DTFT on a rectangular grid (test_oracle_pins)."""
+    rng = np.random.default_rng(4)
+    ny, nx = 24, 40
+    c = np.ascontiguousarray(rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx)))
+    tx = rng.uniform(-nx / 2, nx / 2, 200)
+    ty = rng.uniform(-ny / 2, ny / 2, 200)
+    got = np.empty(200, np.complex128)
+    ref = np.empty(200, np.complex128)
+    args = (c.ctypes.data_as(_dp), nx, ny, tx.ctypes.data_as(_dp), ty.ctypes.data_as(_dp), 200)
+    L.or_nufft2(*args, got.ctypes.data_as(_dp))
+    L.or_dtft2_direct(*args, ref.ctypes.data_as(_dp))
+    return np.abs(got - ref).max() < 1e-10 * np.abs(c).sum() / math.sqrt(c.size)
+
+
+def pin_refocus(L):
+    """A point source refocuses on its own pixel, and a centred one with peak
+    N^4 (test_oracle_pins, whole method against Eq. 3)."""
+    import oracle
+    import synth
+    lam, pitch, n, z = 532e-9, 0.4e-6, 256, 1.0e-3
+    B = oracle.plan_view(lam, pitch, n, n, z)["width"]
+    p = B / n
+    for ix, iy in [(128, 128), (200, 60)]:
+        pts = np.array([[(ix - n / 2) * p, (iy - n / 2) * p, z, 1.0, 0.3]])
+        H = np.ascontiguousarray(synth.hologram(pts, lam, pitch, n, n), np.complex64)
+        field = np.empty((n, n), np.complex128)
+        inten = np.empty((n, n), np.float64)
+        r = L.or_reconstruct(lam, pitch, n, n, H.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             z, 0.0, 0.0, 0.0, 0.0, 0, 0, 1, 0, field.ctypes.data_as(_dp),
+                             inten.ctypes.data_as(_dp))
+        if r:
+            return False
+        j, i = np.unravel_index(np.argmax(inten), inten.shape)
+        if (i, j) != (ix, iy):
+            return False
+        if (ix, iy) == (128, 128) and abs(inten.max() / n ** 4 - 1) >= 5e-3:
+            return False
+    return True
+
+
 # --- mutants ----------------------------------------------------------------
 
 MUTANTS = [
@@ -132,6 +178,15 @@ MUTANTS = [
     # wrong sign: the z term of the point's spectrum phase (wavefront error)
     ("spectrum_phase_sign", "return -(fx * xo + fy * yo + zo * sqrt(",
      "return -(fx * xo + fy * yo - zo * sqrt(", "wavefront"),
+    # transposed operand: the y deconvolution of the NUFFT with the x grid length
+    ("nufft_deconv_axis", "dy[n] = 1.0 / gauss_ft(p->a2, n - ny / 2, p->my);",
+     "dy[n] = 1.0 / gauss_ft(p->a2, n - ny / 2, p->mx);", "nufft"),
+    # wrong sign: the input chirp of Eq. 2 conjugated
+    ("input_chirp_sign", "S[(size_t)m * npx + n] *= inv * (cos(ph) + I * sin(ph));",
+     "S[(size_t)m * npx + n] *= inv * (cos(ph) - I * sin(ph));", "refocus"),
+    # dropped term: one axis of the inverse transform's 1 / (N'_x N'_y)
+    ("idft_normalisation", "const double inv = 1.0 / ((double)npx * npy);",
+     "const double inv = 1.0 / (double)npx;", "refocus"),
 ]
 
 
@@ -145,7 +200,9 @@ def _run_pin(kind, L, golden):
             "output_map": lambda: pin_printed_output_map(L, golden),
             "centred_dft": lambda: pin_centred_dft(L),
             "lerp": lambda: pin_lerp_affine(L),
-            "wavefront": lambda: pin_wavefront_two_ffts(L)}[kind]()
+            "wavefront": lambda: pin_wavefront_two_ffts(L),
+            "nufft": lambda: pin_nufft(L),
+            "refocus": lambda: pin_refocus(L)}[kind]()
 
 
 @pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
