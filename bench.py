@@ -13,7 +13,15 @@ pitch (120 deg FoV), 20000 seeded points in z in [0.6, 3.16] m, full 16384^2
 intensity view at z = 0.8 m.  Inputs (2 GiB hologram, 8.6 GB spectrum) exceed
 L2, so no L2 flush is needed between steps.
 
+Beside the timed step the line carries: e2e (the same step through host
+buffers), the roofline of the dominant kernel, per-stage times, the clocks
+seen, the storage-precision and paper-literal variants, cuFFT (torch.fft)
+timed on the same transform sizes as a comparison, and the FP64 oracle timed
+on the host cores on a bounded sample (cpu_baseline).  Other workloads:
+--workload wa4096 | small512 | strip16k | batch64 | serve | sweep16k.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload W] [--no-cpu-baseline] [--no-cufft]
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
