@@ -39,6 +39,9 @@ def _build(tmp_path, name, old=None, new=None):
     L.or_reconstruct.argtypes = [_d, _d, _i, _i, ctypes.POINTER(ctypes.c_float), _d, _d, _d, _d,
                                  _d, _i, _i, _i, _i, _dp, _dp]
     L.or_reconstruct.restype = _i
+    L.or_hyp2f1.argtypes = [_d]
+    L.or_hyp2f1.restype = _d
+    L.or_output_map_iterative_inverse.argtypes = [_d, _d, _d, _d, _i, _dp, _dp]
     return L
 
 
@@ -159,6 +162,28 @@ def pin_refocus(L):
     return True
 
 
+def pin_hyp2f1(L):
+    """2F1(1/2, 3/4; 3/2; w) against scipy on both sides of w = 1/2."""
+    from scipy.special import hyp2f1
+    for w in (0.1, 0.45, 0.7, 0.95):
+        ref = hyp2f1(0.5, 0.75, 1.5, w)
+        if abs(L.or_hyp2f1(w) - ref) > 1e-13 * ref:
+            return False
+    return True
+
+
+def pin_inverse_iteration(L):
+    """Many steps of the paper's iteration invert Eq. 17 (test_oracle_pins)."""
+    lam, z = 0.5e-6, 1.0
+    for xo, yo in [(0.31, 0.0), (0.2, -0.15)]:
+        xp, yp = _pair(L.or_output_map, lam, z, xo, yo)
+        a, b = _d(), _d()
+        L.or_output_map_iterative_inverse(lam, z, xp, yp, 200, ctypes.byref(a), ctypes.byref(b))
+        if abs(a.value - xo) > 1e-9 or abs(b.value - yo) > 1e-9:
+            return False
+    return True
+
+
 # --- mutants ----------------------------------------------------------------
 
 MUTANTS = [
@@ -184,6 +209,14 @@ MUTANTS = [
     # wrong sign: the input chirp of Eq. 2 conjugated
     ("input_chirp_sign", "S[(size_t)m * npx + n] *= inv * (cos(ph) + I * sin(ph));",
      "S[(size_t)m * npx + n] *= inv * (cos(ph) - I * sin(ph));", "refocus"),
+    # wrong term: a Pochhammer factor of the series (2F1)
+    ("series_pochhammer", "term *= (a + n) * (b + n) / ((c + n) * (n + 1.0)) * w;",
+     "term *= (a + n) * (b + n) / ((c + n + 1.0) * (n + 1.0)) * w;", "hyp2f1"),
+    # wrong sign in the connection formula A&S 15.3.6 (w > 1/2)
+    ("connection_sign", "return t1 + t2;", "return t1 - t2;", "hyp2f1"),
+    # transposed operand: the inverse iteration divides by m_y
+    ("inverse_iteration_axis", "double xn = xop * R / (z * mx), yn = yop * R / (z * my);",
+     "double xn = xop * R / (z * my), yn = yop * R / (z * mx);", "inverse"),
     # dropped term: one axis of the inverse transform's 1 / (N'_x N'_y)
     ("idft_normalisation", "const double inv = 1.0 / ((double)npx * npy);",
      "const double inv = 1.0 / (double)npx;", "refocus"),
@@ -202,7 +235,9 @@ def _run_pin(kind, L, golden):
             "lerp": lambda: pin_lerp_affine(L),
             "wavefront": lambda: pin_wavefront_two_ffts(L),
             "nufft": lambda: pin_nufft(L),
-            "refocus": lambda: pin_refocus(L)}[kind]()
+            "refocus": lambda: pin_refocus(L),
+            "hyp2f1": lambda: pin_hyp2f1(L),
+            "inverse": lambda: pin_inverse_iteration(L)}[kind]()
 
 
 @pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
