@@ -42,6 +42,8 @@ def _build(tmp_path, name, old=None, new=None):
     L.or_hyp2f1.argtypes = [_d]
     L.or_hyp2f1.restype = _d
     L.or_output_map_iterative_inverse.argtypes = [_d, _d, _d, _d, _i, _dp, _dp]
+    L.or_nice.argtypes = [ctypes.c_int64]
+    L.or_nice.restype = ctypes.c_int64
     return L
 
 
@@ -184,6 +186,22 @@ def pin_inverse_iteration(L):
     return True
 
 
+def pin_nice(L):
+    """N' = the smallest 64 * 2^a * {1, 3, 5, 9, 15, 45} >= n (test_oracle_pins)."""
+    def ok(c):
+        if c % 64:
+            return False
+        c //= 64
+        while c % 2 == 0:
+            c //= 2
+        return c in (1, 3, 5, 9, 15, 45)
+    for n in [1, 63, 65, 587, 4439, 7926, 22112, 30000]:
+        m = L.or_nice(n)
+        if m < n or not ok(m) or any(ok(c) for c in range(n, m)):
+            return False
+    return True
+
+
 # --- mutants ----------------------------------------------------------------
 
 MUTANTS = [
@@ -217,6 +235,9 @@ MUTANTS = [
     # transposed operand: the inverse iteration divides by m_y
     ("inverse_iteration_axis", "double xn = xop * R / (z * mx), yn = yop * R / (z * my);",
      "double xn = xop * R / (z * my), yn = yop * R / (z * mx);", "inverse"),
+    # dropped case: the factor 5 of the FFT sizes (planner)
+    ("nice_no_factor5", "for (int c = 0; c <= 1; ++c) {", "for (int c = 0; c <= 0; ++c) {",
+     "nice"),
     # dropped term: one axis of the inverse transform's 1 / (N'_x N'_y)
     ("idft_normalisation", "const double inv = 1.0 / ((double)npx * npy);",
      "const double inv = 1.0 / (double)npx;", "refocus"),
@@ -237,7 +258,8 @@ def _run_pin(kind, L, golden):
             "nufft": lambda: pin_nufft(L),
             "refocus": lambda: pin_refocus(L),
             "hyp2f1": lambda: pin_hyp2f1(L),
-            "inverse": lambda: pin_inverse_iteration(L)}[kind]()
+            "inverse": lambda: pin_inverse_iteration(L),
+            "nice": lambda: pin_nice(L)}[kind]()
 
 
 @pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
