@@ -28,6 +28,10 @@
  * (8 bytes per pixel).  cuda_stream is a cudaStream_t (NULL = legacy
  * default stream).  Calls are asynchronous on that stream unless stated.
  *
+ * Host-only calls (no GPU work, no allocation): nufds_view_plan,
+ * nufds_output_map, nufds_output_map_inverse, nufds_wavefront_error,
+ * nufds_status_string.
+ *
  * Errors.  Every int-returning call returns NUFDS_OK (0) or a negative code;
  * nufds_status_string() names it.  No C++ exception crosses the ABI.  A plan
  * is used by one host thread at a time; different plans are independent.
