@@ -28,7 +28,7 @@
  * (8 bytes per pixel).  cuda_stream is a cudaStream_t (NULL = legacy
  * default stream).  Calls are asynchronous on that stream unless stated.
  *
- * Host-only calls (no GPU work, no allocation): nufds_view_plan,
+ * Host-only calls (no GPU work, no device memory): nufds_view_plan,
  * nufds_output_map, nufds_output_map_inverse, nufds_wavefront_error,
  * nufds_status_string.
  *
