@@ -106,6 +106,28 @@ def test_planner_matches_oracle_random_views(built):
             assert got[k] == ref[k], (it, k)
 
 
+def test_polynomial_planner_matches_oracle(built):
+    """With the paper's polynomial surrogate (plan flag) the planner's Eq. 17
+    uses the surrogate, like the oracle inside its paper_poly context."""
+    rng = np.random.default_rng(2)
+    for it in range(40):
+        n = int(rng.choice([256, 512, 1024]))
+        lam, pitch = 532e-9, float(rng.uniform(0.3e-6, 0.5e-6))
+        z = float(rng.uniform(0.3, 2.0))
+        B = oracle.plan_view(lam, pitch, n, n, z)["width"]
+        p = B / n
+        ox, oy = int(rng.integers(8, n)), int(rng.integers(8, n))
+        cx = float(rng.uniform(-0.5, 0.5)) * (B - ox * p)
+        cy = float(rng.uniform(-0.5, 0.5)) * (B - oy * p)
+        v = nf.View(z=z, center_x=cx, center_y=cy, width=ox * p, height=oy * p, out_nx=ox,
+                    out_ny=oy)
+        got = nf.view_plan(lam, pitch, n, n, v, flags=nf.FLAG_PAPER_POLY_M)
+        with oracle.paper_poly(lam, pitch):
+            ref = oracle.plan_view(lam, pitch, n, n, z, cx, cy, ox * p, oy * p, ox, oy)
+        for k in ["k_lo_x", "k_hi_x", "k_lo_y", "k_hi_y", "np_x", "np_y"]:
+            assert got[k] == ref[k], (it, k)
+
+
 def test_plain_frt_planner_matches_oracle(built):
     """Plain Fresnel transform views (no stretch): band from the view's own
     extent, same integers as the oracle's stretch = 0 planner."""
