@@ -202,6 +202,24 @@ def pin_nice(L):
     return True
 
 
+def pin_fresnel(L):
+    """Plain Fresnel-transform field against the closed-form Fresnel integral of
+    a Gaussian beam, no fitted constant (test_oracle_pins)."""
+    from test_oracle_pins import FRESNEL_CASES, gaussian_beam_case
+    for case in FRESNEL_CASES:
+        H, a, ref = gaussian_beam_case(case)
+        H = np.ascontiguousarray(H, np.complex64)
+        field = np.empty(ref.shape, np.complex128)
+        inten = np.empty(ref.shape, np.float64)
+        r = L.or_reconstruct(a["lam"], a["pitch"], H.shape[1], H.shape[0],
+                             H.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a["z"], a["cx"],
+                             a["cy"], a["w"], a["h"], a["ox"], a["oy"], 0, 0,
+                             field.ctypes.data_as(_dp), inten.ctypes.data_as(_dp))
+        if r or not np.linalg.norm(field - ref) < 1e-6 * np.linalg.norm(ref):
+            return False
+    return True
+
+
 # --- mutants ----------------------------------------------------------------
 
 MUTANTS = [
@@ -241,6 +259,12 @@ MUTANTS = [
     # dropped term: one axis of the inverse transform's 1 / (N'_x N'_y)
     ("idft_normalisation", "const double inv = 1.0 / ((double)npx * npy);",
      "const double inv = 1.0 / (double)npx;", "refocus"),
+    # wrong sign: the output chirp of Eq. 2 conjugated (step O9)
+    ("output_chirp_sign", "cplx O = (cos(ph) + I * sin(ph)) * P[o];",
+     "cplx O = (cos(ph) - I * sin(ph)) * P[o];", "fresnel"),
+    # dropped term: no output chirp at all (step O9)
+    ("output_chirp_dropped", "cplx O = (cos(ph) + I * sin(ph)) * P[o];", "cplx O = P[o];",
+     "fresnel"),
 ]
 
 
@@ -259,7 +283,8 @@ def _run_pin(kind, L, golden):
             "refocus": lambda: pin_refocus(L),
             "hyp2f1": lambda: pin_hyp2f1(L),
             "inverse": lambda: pin_inverse_iteration(L),
-            "nice": lambda: pin_nice(L)}[kind]()
+            "nice": lambda: pin_nice(L),
+            "fresnel": lambda: pin_fresnel(L)}[kind]()
 
 
 @pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
