@@ -9,16 +9,22 @@ per-geometry FP64 tables (the paper's initialisation steps) are built once,
 before the timed region, and reported as init_ms.
 
 Default workload: 16384^2 complex64 point-cloud hologram, 532 nm, 0.307 um
-pitch (120 deg FoV), 20000 seeded points in z in [0.6, 3.16] m, full 16384^2
-intensity view at z = 0.8 m.  Inputs (2 GiB hologram, 8.6 GB spectrum) exceed
-L2, so no L2 flush is needed between steps.
+pitch (120 deg FoV), 20000 seeded points in z in [2, 10] mm, full 16384^2
+intensity view at z = 6 mm, plus its 16 seeded 2048^2 partial views.  Inputs
+(2 GiB hologram, 8.6 GB spectrum) exceed L2, so no L2 flush is needed between
+steps.
 
 Beside the timed step the line carries: e2e (the same step through host
-buffers), the roofline of the dominant kernel, per-stage times, the clocks
-seen, the storage-precision and paper-literal variants, cuFFT (torch.fft)
-timed on the same transform sizes as a comparison, and the FP64 oracle timed
-on the host cores on a bounded sample (cpu_baseline).  Other workloads:
---workload wa4096 | small512 | strip16k | batch64 | serve | sweep16k.
+buffers), the roofline (the minimum schedule's bytes over the step time and
+over the dominant kernel's time, with the design's own bytes beside them),
+p50/p99 of the step and of a view on the loaded hologram, per-stage times,
+the clocks seen, the 16 partial views, the storage-precision and
+paper-literal variants, cuFFT (torch.fft) timed on the same transform sizes
+as a comparison, and the FP64 oracle timed on the host cores on a bounded
+sample (cpu_baseline).  Other workloads: --workload wa4096 | small512 (the
+stated 4096^2 at 3 mm and 512^2 at 1 mm), uwa16k-paper-depths |
+wa4096-paper-depths | small512-paper-depths (the paper's metre depths),
+strip16k | batch64 | serve | sweep16k.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload W] [--no-cpu-baseline] [--no-cufft]
@@ -43,10 +49,49 @@ METRIC = "16K UWA Mpix/s & HBM roofline frac vs plain FP32; p50/p99 view latency
 FALLBACK_HBM_GBS = 6800.0
 
 
+WORKLOADS = ("uwa16k", "wa4096", "small512", "uwa16k-paper-depths", "wa4096-paper-depths",
+             "small512-paper-depths", "strip16k")
+
+
 def _workload(name):
     from synth import configs
-    return {"uwa16k": configs.UWA_16K, "wa4096": configs.WA_4096, "small512": configs.SMALL_512,
+    return {"uwa16k": configs.UWA_16K_MM, "wa4096": configs.WA_4096_MM,
+            "small512": configs.SMALL_512_MM, "uwa16k-paper-depths": configs.UWA_16K,
+            "wa4096-paper-depths": configs.WA_4096, "small512-paper-depths": configs.SMALL_512,
             "strip16k": configs.STRIP_16K}[name]
+
+
+def sec8d_bytes(n, ny, npx, npy, ox, oy, eb=8):
+    """Minimum bytes of one cold view (hot-path scope table, measurement row):
+    read the hologram (8 B per sample), the x<->y exchange of its FFT2 (write +
+    read), the cached spectrum (write + read), the y<->x exchange of the
+    Fresnel transform (write + read) and the f32 intensity written; eb is the
+    storage of a complex intermediate (8 for c64, 4 for FP16/BF16)."""
+    a, ap = n * ny, npx * npy
+    return 8.0 * a + 2 * eb * a + 2 * eb * a + 2 * eb * ap + 4.0 * ox * oy
+
+
+def sec8d_share(stage, n, ny, npx, npy, ox, oy, eb=8):
+    """Each term of sec8d_bytes credited to the kernel that must move it: the
+    hologram read and the exchange write to the x pass of the spectrum, the
+    exchange read and the spectrum write to its y pass, the spectrum read to
+    the stretch (plus its S write, which the minimum schedule fuses into the y
+    pass), the exchange write and read to the two Fresnel passes, the image to
+    the remap; the transposes move nothing the minimum schedule needs."""
+    a, ap = n * ny, npx * npy
+    return {"pad_rows_x": 8.0 * a + eb * a, "pad_rows_y": 2.0 * eb * a,
+            "stretch": eb * a + eb * ap, "view_rows_y": eb * ap, "view_rows_x": eb * ap,
+            "remap": 4.0 * ox * oy}.get(stage, 0.0)
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q / 100.0
+    lo = int(math.floor(k))
+    hi = min(lo + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
 L2_BYTES = 129 * 2 ** 20
@@ -333,15 +378,22 @@ def run_ours(args, w):
         torch.cuda.synchronize()
         small_ms = sum(a.elapsed_time(b) for a, b in pairs)
     else:
-        ev0.record(stream)
-        for _ in range(args.steps):
+        # one event between consecutive steps: the step times give p50/p99
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        marks[0].record(stream)
+        for k in range(args.steps):
             step()
-        ev1.record(stream)
+            marks[k + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     launches = nf.launch_count()
     plan.profile(False)
-    ms = (small_ms if _small(w) else ev0.elapsed_time(ev1)) / args.steps
+    if _small(w):
+        step_ms = [a.elapsed_time(b) for a, b in pairs]
+        ms = small_ms / args.steps
+    else:
+        step_ms = [marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps)]
+        ms = marks[0].elapsed_time(marks[-1]) / args.steps
     clk = clocks.stop()
     stats = plan.profile_read()
 
@@ -376,17 +428,47 @@ def run_ours(args, w):
     value_e2e = whole_job_rate(pix, ms_e2e, world) / 1e6
 
     dom = max(stats, key=lambda s: s["total_ms"])
-    per_launch_bytes = dom["bytes"] / dom["launches"]
     per_launch_ms = dom["total_ms"] / dom["launches"]
-    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    geo = (n, ny, info["np_x"], info["np_y"], info["out_nx"], info["out_ny"])
+    # algorithmic bytes: the minimum schedule's (hot-path scope table, measurement
+    # row), not this design's; the design's own modelled bytes sit beside them
+    dom_bytes = sec8d_share(dom["name"], *geo)
+    design_bytes = dom["bytes"] / dom["launches"]
+    achieved = dom_bytes / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
+    step_bytes = sec8d_bytes(*geo)
+    step_gbs = step_bytes / (ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": _traffic(dom["name"]),
-            "bytes_per_launch": per_launch_bytes, "ms_per_launch": round(per_launch_ms, 4)}
+            "algorithmic_bytes_per_launch": dom_bytes, "ms_per_launch": round(per_launch_ms, 4),
+            "design_bytes_per_launch": design_bytes,
+            "design_frac": round(design_bytes / (per_launch_ms * 1e-3) / 1e9 / peak, 4),
+            "whole_step": {"algorithmic_bytes": step_bytes, "achieved": round(step_gbs, 1),
+                           "frac": round(step_gbs / peak, 4),
+                           "frac_of_8tbs": round(step_gbs / 8000.0, 4),
+                           "design_bytes": sum(s["bytes"] for s in stats) / args.steps}}
     stages = {s["name"]: {"ms_per_step": round(s["total_ms"] / args.steps, 4),
-                          "GBps": round(s["bytes"] / (s["total_ms"] * 1e-3) / 1e9, 1)
+                          "design_GBps": round(s["bytes"] / (s["total_ms"] * 1e-3) / 1e9, 1)
+                          if s["total_ms"] > 0 else None,
+                          "algorithmic_GBps": round(sec8d_share(s["name"], *geo) * s["launches"] /
+                                                    (s["total_ms"] * 1e-3) / 1e9, 1)
                           if s["total_ms"] > 0 else None} for s in stats}
+    # latency of a view on the loaded hologram (cached spectrum), call by call
+    vl = []
+    plan.load(d_holo)
+    for _ in range(max(5, min(args.steps, 30))):
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.reconstruct(view, out)
+        b2.record(stream)
+        vl.append((a, b2))
+    torch.cuda.synchronize()
+    vl = [a.elapsed_time(b2) for a, b2 in vl]
+    latency = {"step_ms_p50": round(_pct(step_ms, 50), 4), "step_ms_p99": round(_pct(step_ms, 99), 4),
+               "view_ms_p50": round(_pct(vl, 50), 4), "view_ms_p99": round(_pct(vl, 99), 4),
+               "what": "step = new hologram + full view, one event pair per timed step; view = "
+                       "reconstruct on the loaded hologram (cached spectrum), %d calls" % len(vl)}
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -397,7 +479,8 @@ def run_ours(args, w):
                     "d2h_bytes_per_step": int(h_out[0].numel() * h_out[0].element_size()),
                     "pipeline": "copy-in of step i+1 and copy-out of step i-1 overlap step i "
                                 "(two copy streams, double-buffered staging; HostPipeline)"},
-            "roofline": roof, "stages": stages, "clocks": clk, "gpu_launches": int(launches),
+            "roofline": roof, "latency": latency, "stages": stages, "clocks": clk,
+            "gpu_launches": int(launches),
             "init_ms": round(init_ms, 1), "input_gen_s": round(gen_s, 2)}
     # storage-precision variants of the same step (FP32 arithmetic), with the
     # relative L2 of their intensity against the FP32 path's
@@ -498,6 +581,43 @@ def run_ours(args, w):
         del pout
     except RuntimeError as e:
         line["partial_view"] = {"error": str(e).splitlines()[0][:200]}
+    if w.partial_views:
+        # the workload's seeded partial views (on the full view's pixel lattice),
+        # each call timed by its own event pair on the loaded hologram
+        try:
+            plan.load(d_holo)
+            pp_ = info["pitch_out_x_m"]
+            pvs = [nf.View(z=w.z_view, center_x=float(dx) * pp_, center_y=float(dy) * pp_,
+                           width=w.partial_size * pp_, height=w.partial_size * pp_,
+                           out_nx=w.partial_size, out_ny=w.partial_size)
+                   for dx, dy in w.partial_view_offsets()]
+            pouts = [plan.output_like(v) for v in pvs]
+            for v, o in zip(pvs, pouts):
+                plan.reconstruct(v, o)
+            torch.cuda.synchronize()
+            rounds = max(2, min(args.steps // 4, 5))
+            pairs = []
+            for _ in range(rounds):
+                for v, o in zip(pvs, pouts):
+                    a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    plan.reconstruct(v, o)
+                    b2.record(stream)
+                    pairs.append((a, b2))
+            torch.cuda.synchronize()
+            t = [a.elapsed_time(b2) for a, b2 in pairs]
+            tot = sum(t) / rounds
+            nps = sorted({(plan.view_plan(v)["np_x"], plan.view_plan(v)["np_y"]) for v in pvs})
+            line["partial_views_%d" % w.partial_size] = {
+                "views": len(pvs), "size": w.partial_size, "np": [list(x) for x in nps],
+                "ms_per_16_views": round(tot, 3),
+                "views_per_s": round(len(pvs) / (tot * 1e-3), 2),
+                "Mpix_per_s": round(len(pvs) * w.partial_size ** 2 / (tot * 1e-3) / 1e6, 2),
+                "view_ms_p50": round(_pct(t, 50), 4), "view_ms_p99": round(_pct(t, 99), 4),
+                "rounds": rounds}
+            del pouts
+        except RuntimeError as e:
+            line["partial_views_%d" % w.partial_size] = {"error": str(e).splitlines()[0][:200]}
     if not args.no_cufft:
         try:
             line["cufft_comparison"] = cufft_comparison(d_holo, info, stages)
@@ -735,7 +855,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uwa16k",
-                    choices=["uwa16k", "wa4096", "small512", "strip16k", "batch64", "serve", "sweep16k"])
+                    choices=list(WORKLOADS) + ["batch64", "serve", "sweep16k"])
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -534,7 +534,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     sa.prec = P->prec;
     sa.sc_g = scale_ptr(P, 1);
     sa.sc_s = scale_ptr(P, 2);
-    sa.energy = P->prec == NUFDS_FP16_STORE ? P->acc + 2 : nullptr;
+    sa.energy = P->prec == NUFDS_FP16_STORE ? P->acc + kEnergyAcc : nullptr;
     const double np2 = (double)V.npx * V.npy, q = prec_bytes(P->prec) / 8.0;
     const double nbx = (double)(V.khi_x - V.klo_x + 1), nby = (double)(V.khi_y - V.klo_y + 1);
     // algorithmic bytes of the gather: table entries of the band, the part of
@@ -543,7 +543,8 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     const double st_bytes = 12.0 * nbx * nby + 32.0 * q * P->nx * P->ny * g_frac + 8.0 * q * np2;
     if (!(sw && sw->same(V))) {  // a sweep reuses the band of an earlier depth
         if (P->prec == NUFDS_FP16_STORE &&
-            cudaMemsetAsync(P->acc + 2, 0, sizeof(double), st) != cudaSuccess)
+            cudaMemsetAsync(P->acc + kEnergyAcc, 0, kEnergySlots * sizeof(double), st) !=
+                cudaSuccess)
             return NUFDS_ECUDA;
         if ((rc = stage(P, ST_STRETCH, st_bytes, st, [&] { return launch_stretch(sa, st); })))
             return rc;
@@ -992,7 +993,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         sa.prec = prec;
         sa.sc_g = scG;
         sa.sc_s = scS;
-        sa.energy = prec == NUFDS_FP16_STORE ? g.acc + 2 : nullptr;
+        sa.energy = prec == NUFDS_FP16_STORE ? g.acc + kEnergyAcc : nullptr;
         hsoff[i] = tst;
         tst += stretch_tiles(V.npx, V.npy);
         RowItem &ry = items_y[i];
@@ -1120,7 +1121,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
                 rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px, V.py,
                                         V.ox, V.oy, g.rmb, g.rmf, st, V.plain, P->geom.mf);
             if (!rc && prec == NUFDS_FP16_STORE &&
-                cudaMemsetAsync(g.acc, 0, 4 * sizeof(double), st) != cudaSuccess)
+                cudaMemsetAsync(g.acc, 0, (kEnergyAcc + kEnergySlots) * sizeof(double), st) !=
+                    cudaSuccess)
                 rc = NUFDS_ECUDA;
         }
         const char *where = "tables";

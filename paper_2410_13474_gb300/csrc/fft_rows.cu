@@ -1157,9 +1157,11 @@ __global__ void k_scales_load(float *sc, const double *acc, int nx, int ny, doub
     sc[2] = pow2_scale(k2 * bG);
 }
 
-//   |T_T| <= sqrt(2) dy' ||S||,  |Q| <= 2 dx' dy' ||S||  (acc[2] = ||S||^2)
+//   |T_T| <= sqrt(2) dy' ||S||,  |Q| <= 2 dx' dy' ||S||  (||S||^2 in kEnergySlots parts)
 __global__ void k_scales_view(float *sc, const double *acc, double dxp, double dyp) {
-    const double nS = sqrt(acc[2]);
+    double e = 0;
+    for (int k = 0; k < kEnergySlots; ++k) e += acc[kEnergyAcc + k];
+    const double nS = sqrt(e);
     sc[3] = pow2_scale(sqrt(2.0) * dyp * nS);
     sc[4] = sc[3];
     sc[5] = pow2_scale(2.0 * dxp * dyp * nS);

@@ -339,10 +339,20 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
         acc = make_float2(acc.x * ginv, acc.y * ginv);
     }
     if (inside) st_c((T *)a.S, (long)jx * a.npy + jy, acc, ssc);
-    if (a.energy) {  // uniform over the launch; every lane reaches the shuffles
+    if (a.energy) {  // uniform over the launch; every thread reaches the barrier
+        // one atomic per CTA, spread over kEnergySlots addresses (a single
+        // address serialises the atomics of every warp of the launch)
+        __shared__ double red[8];
         double e = (double)acc.x * acc.x + (double)acc.y * acc.y;
         for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(a.energy, e);
+        const int wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+        if ((threadIdx.x & 31) == 0) red[wid] = e;
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            double t = 0;
+            for (int k = 0; k < (int)(blockDim.x * blockDim.y) >> 5; ++k) t += red[k];
+            atomicAdd(a.energy + ((bx + by) & (kEnergySlots - 1)), t);
+        }
     }
 }
 

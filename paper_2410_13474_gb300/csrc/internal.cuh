@@ -263,7 +263,8 @@ struct StretchArgs {
     void *S;                // output, layout [jx][jy], npx x npy
     int prec;               // storage of G and S
     const float *sc_g, *sc_s;
-    double *energy;         // if not null: += sum |S|^2 (before storage rounding)
+    double *energy;         // if not null: sum |S|^2 (before storage rounding) added over
+                            // energy[0 .. kEnergySlots), zeroed by the caller
     int plain;              // 1: no stretch, S(f'_k) = DTFT at f = f'_k (plain FrT)
     int linear;             // 1: bilinear on the unpadded DFT grid (G's even samples of
                             //    the hologram loaded without deapodisation)
@@ -301,7 +302,10 @@ inline int remap_tiles(int ox, int oy) { return ((ox + 31) / 32) * ((oy + 7) / 8
 // Frobenius norm, which Parseval gives for every DFT stage):
 //   sc[0] T1, sc[1] G, sc[2] S, sc[3] T_T, sc[4] T, sc[5] Q; each the largest
 //   power of two with scale * bound <= 2^15.  acc[] (device doubles): [0], [1]
-//   weighted hologram energies (launch_norms), [2] ||S||^2 (the stretch).
+//   weighted hologram energies (launch_norms), [kEnergyAcc, kEnergyAcc +
+//   kEnergySlots) partial sums of ||S||^2 (the stretch).
+constexpr int kEnergySlots = 16;
+constexpr int kEnergyAcc = 8;
 int launch_norms(const float2 *H, int nx, int ny, const double *dx, const double *dy, double *acc,
                  cudaStream_t st);
 int launch_scales_load(float *sc, const double *acc, int nx, int ny, double k2, cudaStream_t st);

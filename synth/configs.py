@@ -83,7 +83,25 @@ UWA_16K = Workload("pointcloud-16384-532nm-0.307um-20000pt", 16384, LAMBDA_532, 
 STRIP_16K = Workload("strip-16384x2048-532nm-0.307um-2000pt", 16384, LAMBDA_532, 0.307e-6,
                      2000, (0.6, 3.16), (0.5, 1.0), 0.8, seed=20241023, ny=2048)
 
-ALL = {w.name: w for w in (SMALL_512, WA_4096, UWA_16K, STRIP_16K)}
+# The same three shapes with the point depths and viewing distances stated for
+# the benchmark, in millimetres: the hologram is then not small against the
+# object distance (5 mm aperture at 6 mm for 16K), outside the regime where the
+# method's paraxial premise holds, so these are parity and throughput cases,
+# not refocus cases.
+# 512^2, 0.4 um (83 deg), 8 unit-amplitude points, z in [0.5, 2] mm, view at 1 mm.
+SMALL_512_MM = Workload("pointcloud-512-532nm-0.4um-8pt-z0.5-2mm", 512, LAMBDA_532, 0.4e-6, 8,
+                        (0.5e-3, 2e-3), (1.0, 1.0), 1e-3, seed=20241101)
+# 4096^2, 0.5 um (64 deg), 2000 points, z in [1, 5] mm, amplitudes U[0.5, 1], view at 3 mm.
+WA_4096_MM = Workload("pointcloud-4096-532nm-0.5um-2000pt-z1-5mm", 4096, LAMBDA_532, 0.5e-6,
+                      2000, (1e-3, 5e-3), (0.5, 1.0), 3e-3, seed=20241102)
+# 16384^2, 0.307 um (120 deg), 20000 points, z in [2, 10] mm, amplitudes U[0.5, 1],
+# full view at 6 mm (the middle of the depth range) plus 16 partial views of 2048^2.
+UWA_16K_MM = Workload("pointcloud-16384-532nm-0.307um-20000pt-z2-10mm", 16384, LAMBDA_532,
+                      0.307e-6, 20000, (2e-3, 10e-3), (0.5, 1.0), 6e-3, seed=20241103,
+                      partial_views=16, partial_size=2048)
+
+ALL = {w.name: w for w in (SMALL_512, WA_4096, UWA_16K, STRIP_16K, SMALL_512_MM, WA_4096_MM,
+                           UWA_16K_MM)}
 
 
 @dataclass(frozen=True)

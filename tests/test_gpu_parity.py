@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from synth.configs import SMALL_512, WA_4096
+from synth.configs import SMALL_512, SMALL_512_MM, WA_4096, WA_4096_MM
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -142,7 +142,27 @@ def test_point_source_refocus_and_peak(nf):
 
 @pytest.mark.slow
 def test_pointcloud_4096_full_view(nf):
-    """The wide-angle FP32 workload at full size (4096^2, 2000 points, z = 3 mm)."""
+    """The wide-angle FP32 workload at full size at the paper's depths (4096^2,
+    2000 points at 0.5-1.5 m, full view at 0.85 m)."""
     w = WA_4096
+    H = w.make_hologram()
+    check(nf, H, w.wavelength, w.pitch, dict(z=w.z_view))
+
+
+def test_pointcloud_512_mm_full_view(nf):
+    """512^2 at 0.4 um, 8 unit-amplitude points at z in [0.5, 2] mm, full view
+    at z = 1 mm (N' = 640), field within 1e-5 of the oracle."""
+    w = SMALL_512_MM
+    H = w.make_hologram()
+    e, p = check(nf, H, w.wavelength, w.pitch, dict(z=w.z_view))
+    assert p > 60
+
+
+@pytest.mark.slow
+def test_pointcloud_4096_mm_full_view(nf):
+    """The wide-angle FP32 workload at its stated depths: 4096^2 at 0.5 um,
+    2000 points at z in [1, 5] mm, full view at z = 3 mm (N' = 4608), field
+    within 1e-5 of the oracle."""
+    w = WA_4096_MM
     H = w.make_hologram()
     check(nf, H, w.wavelength, w.pitch, dict(z=w.z_view))

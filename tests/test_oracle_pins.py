@@ -226,9 +226,10 @@ def test_nice_sizes():
 
 
 def test_view_plan_sizes_of_the_workloads():
-    from synth.configs import SMALL_512, WA_4096, UWA_16K
-    expect = {SMALL_512.name: 640, WA_4096.name: 4608, UWA_16K.name: 23040}
-    for w in (SMALL_512, WA_4096, UWA_16K):
+    from synth.configs import SMALL_512, WA_4096, UWA_16K, SMALL_512_MM, WA_4096_MM, UWA_16K_MM
+    expect = {SMALL_512.name: 640, WA_4096.name: 4608, UWA_16K.name: 23040,
+              SMALL_512_MM.name: 640, WA_4096_MM.name: 4608, UWA_16K_MM.name: 23040}
+    for w in (SMALL_512, WA_4096, UWA_16K, SMALL_512_MM, WA_4096_MM, UWA_16K_MM):
         p = oracle.plan_view(w.wavelength, w.pitch, w.n, w.n, w.z_view)
         assert p["np_x"] == p["np_y"] == expect[w.name]
         assert p["k_lo_x"] == -p["k_hi_x"] - 1 or p["k_lo_x"] == -p["k_hi_x"]
