@@ -66,6 +66,10 @@ def lib():
             L.or_reconstruct.argtypes = [_d, _d, _i, _i, _fp, _d, _d, _d, _d, _d, _i, _i, _i, _i,
                                          _dp, _dp]
             L.or_reconstruct.restype = _i
+            L.or_reconstruct_views.argtypes = [_d, _d, _i, _i, _fp, _i, _dp, _dp, _dp, _dp, _dp,
+                                               ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _i,
+                                               ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
+            L.or_reconstruct_views.restype = _i
             L.or_num_threads.restype = _i
             L.or_set_paper_poly.argtypes = [_i, _d, _d, _dp]
             L.or_set_paper_poly.restype = None
@@ -208,6 +212,36 @@ def reconstruct(holo: np.ndarray, wavelength: float, pitch: float, z: float, cx=
     if r:
         raise ValueError("invalid view")
     return field, inten
+
+
+def reconstruct_views(holo: np.ndarray, wavelength: float, pitch: float, views, stretch=True,
+                      threads=0):
+    """Several views of one hologram, each a dict(z, cx, cy, w, h, ox, oy) as the
+    arguments of reconstruct; returns a list of (field, intensity).  Same
+    results as one reconstruct call per view; step two's gridded transform of
+    the hologram is shared."""
+    holo = np.ascontiguousarray(holo, np.complex64)
+    ny, nx = holo.shape
+    nv = len(views)
+    cols = {k: np.array([float(v.get(k, 0.0)) for v in views]) for k in ("z", "cx", "cy", "w", "h")}
+    oxs = (_i * nv)(*[int(v.get("ox", 0)) for v in views])
+    oys = (_i * nv)(*[int(v.get("oy", 0)) for v in views])
+    outs = []
+    for v in views:
+        p = plan_view(wavelength, pitch, nx, ny, v["z"], v.get("cx", 0.0), v.get("cy", 0.0),
+                      v.get("w", 0.0), v.get("h", 0.0), v.get("ox", 0), v.get("oy", 0),
+                      int(stretch))
+        outs.append((np.empty((p["out_ny"], p["out_nx"]), np.complex128),
+                     np.empty((p["out_ny"], p["out_nx"]), np.float64)))
+    fp = (_dp * nv)(*[_ptr(f) for f, _ in outs])
+    ip = (_dp * nv)(*[_ptr(i) for _, i in outs])
+    r = lib().or_reconstruct_views(wavelength, pitch, nx, ny, _ptr(holo, _fp), nv,
+                                   _ptr(cols["z"]), _ptr(cols["cx"]), _ptr(cols["cy"]),
+                                   _ptr(cols["w"]), _ptr(cols["h"]), oxs, oys, int(stretch),
+                                   int(threads), fp, ip)
+    if r:
+        raise ValueError("invalid view")
+    return outs
 
 
 class paper_poly:

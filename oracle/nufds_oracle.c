@@ -758,12 +758,11 @@ static void off_grid(const double *c, int nx, int ny, const double *tx, const do
  * NULL) and intensity (float64, may be NULL).  threads <= 0: OpenMP default.
  * Returns 0 or -1.
  */
-int or_reconstruct(double lam, double pitch, int nx, int ny, const float *holo, double z,
-                   double cx, double cy, double w, double h, int ox_in, int oy_in, int stretch,
-                   int threads, double *field_out, double *intensity_out) {
-#ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#endif
+/* One view of the hologram H (FP64, ny x nx); gH, if not NULL, is H's
+ * gridding plan shared by several views (the ideal resampling only). */
+static int recon_view(double lam, double pitch, int nx, int ny, const cplx *H, const gg_plan *gH,
+                      double z, double cx, double cy, double w, double h, int ox_in, int oy_in,
+                      int stretch, double *field_out, double *intensity_out) {
     int64_t iv[8];
     double dv[4];
     if (or_plan_view_ex(lam, pitch, nx, ny, z, cx, cy, w, h, ox_in, oy_in, stretch, iv, dv))
@@ -775,11 +774,6 @@ int or_reconstruct(double lam, double pitch, int nx, int ny, const float *holo, 
     const int64_t kcy = (int64_t)floor(0.5 * (double)(klo_y + khi_y));
     const double px = dv[0], py = dv[1];
     const double dfx = 1.0 / (nx * pitch), dfy = 1.0 / (ny * pitch); /* stretched lattice */
-
-    /* O0: promote the hologram to FP64 */
-    size_t nh = (size_t)nx * ny;
-    cplx *H = (cplx *)malloc(sizeof(cplx) * nh);
-    for (size_t i = 0; i < nh; ++i) H[i] = (double)holo[2 * i] + I * (double)holo[2 * i + 1];
 
     /* Step two: S(f'_k) = DTFT of H at the pulled-back f(f'_k); zero outside
      * the band, where no pre-image exists, or outside |f| <= 1/(2 pitch). */
@@ -810,10 +804,14 @@ int or_reconstruct(double lam, double pitch, int nx, int ny, const float *holo, 
         }
     }
     cplx *S = (cplx *)malloc(sizeof(cplx) * nS);
-    off_grid((const double *)H, nx, ny, tx, ty, (int64_t)nS, (double *)S);
+    if (gH) {
+#pragma omp parallel for schedule(static)
+        for (int64_t t = 0; t < (int64_t)nS; ++t) S[t] = gg_eval(gH, tx[t], ty[t]);
+    } else {
+        off_grid((const double *)H, nx, ny, tx, ty, (int64_t)nS, (double *)S);
+    }
     for (size_t s = 0; s < nS; ++s)
         if (!keep[s]) S[s] = 0;
-    free(H);
     free(keep);
     free(tx);
     free(ty);
@@ -868,6 +866,57 @@ int or_reconstruct(double lam, double pitch, int nx, int ny, const float *holo, 
     free(xq);
     free(yq);
     return 0;
+}
+
+/* O0: the c64 hologram as the GPU receives it, promoted to FP64 */
+static cplx *promote(const float *holo, int nx, int ny) {
+    size_t nh = (size_t)nx * ny;
+    cplx *H = (cplx *)malloc(sizeof(cplx) * nh);
+    for (size_t i = 0; i < nh; ++i) H[i] = (double)holo[2 * i] + I * (double)holo[2 * i + 1];
+    return H;
+}
+
+int or_reconstruct(double lam, double pitch, int nx, int ny, const float *holo, double z,
+                   double cx, double cy, double w, double h, int ox_in, int oy_in, int stretch,
+                   int threads, double *field_out, double *intensity_out) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    cplx *H = promote(holo, nx, ny);
+    int r = recon_view(lam, pitch, nx, ny, H, NULL, z, cx, cy, w, h, ox_in, oy_in, stretch,
+                       field_out, intensity_out);
+    free(H);
+    return r;
+}
+
+/*
+ * Several views of one hologram (arrays of nv view arguments and output
+ * pointers, as in or_reconstruct).  The same arithmetic as nv calls of
+ * or_reconstruct; the gridded oversampled transform of the hologram that
+ * step two evaluates is computed once and shared by the views.
+ */
+int or_reconstruct_views(double lam, double pitch, int nx, int ny, const float *holo, int nv,
+                         const double *z, const double *cx, const double *cy, const double *w,
+                         const double *h, const int *ox, const int *oy, int stretch, int threads,
+                         double *const *field_out, double *const *intensity_out) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    cplx *H = promote(holo, nx, ny);
+    gg_plan gH;
+    const gg_plan *pg = NULL;
+    if (!g_linear) {
+        gg_prepare(&gH, H, nx, ny);
+        pg = &gH;
+    }
+    int r = 0;
+    for (int v = 0; v < nv && !r; ++v)
+        r = recon_view(lam, pitch, nx, ny, H, pg, z[v], cx[v], cy[v], w[v], h[v], ox[v], oy[v],
+                       stretch, field_out ? field_out[v] : NULL,
+                       intensity_out ? intensity_out[v] : NULL);
+    if (pg) free(gH.grid);
+    free(H);
+    return r;
 }
 
 /* Number of OpenMP threads the oracle will use. */

@@ -372,6 +372,20 @@ def test_two_points_focus_at_their_own_depths():
     assert I1[128, 220] > 20 * I2[128, int(round(n / 2 + x1 / p2))]
 
 
+def test_reconstruct_views_equals_single_views():
+    """The multi-view entry point (one gridded transform of the hologram shared
+    by the views) returns exactly what one call per view returns."""
+    rng = np.random.default_rng(8)
+    H = (rng.standard_normal((96, 128)) + 1j * rng.standard_normal((96, 128))).astype(np.complex64)
+    lam, pitch = 532e-9, 0.4e-6
+    vs = [dict(z=0.4e-3), dict(z=0.5e-3, cx=2e-5, cy=-1e-5, w=3e-5, h=2e-5, ox=30, oy=21)]
+    for v, (f, i) in zip(vs, oracle.reconstruct_views(H, lam, pitch, vs)):
+        f1, i1 = oracle.reconstruct(H, lam, pitch, v["z"], v.get("cx", 0.0), v.get("cy", 0.0),
+                                    v.get("w", 0.0), v.get("h", 0.0), v.get("ox", 0),
+                                    v.get("oy", 0))
+        assert np.array_equal(f, f1) and np.array_equal(i, i1)
+
+
 def test_partial_view_covering_the_window_equals_full_view():
     lam, pitch, n, z = GEOM["lam"], GEOM["pitch"], 128, 1.0e-3
     rng = np.random.default_rng(5)
