@@ -10,6 +10,10 @@ size on the GPU.
 * A 1024^2 partial view of a 16K hologram against the FP64 oracle at 1025
   sampled pixels, stored by tests/golden/make_uwa16k_crop.py (which runs the
   oracle once on the host: its 16K gridding FFT takes minutes).
+* The 16 seeded 2048^2 partial views of the 16K workload at its stated depths
+  (20000 points at 2-10 mm, views at 6 mm, N' = 8192 each) against the FP64
+  oracle at 257 sampled pixels per view, stored by
+  tests/golden/make_uwa16k_mm_views.py.
 """
 import importlib.util
 import os
@@ -94,3 +98,57 @@ def test_uwa16k_partial_view_vs_oracle_samples(nf):
     assert e <= TOL, e
     # the oracle's brightest pixel (last row) is the GPU's brightest too
     assert np.unravel_index(int(np.argmax(np.abs(f))), f.shape) == (j[-1], i[-1])
+
+
+def _mm_views_module():
+    spec = importlib.util.spec_from_file_location(
+        "make_uwa16k_mm_views", os.path.join(HERE, "golden", "make_uwa16k_mm_views.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def read_mm_view_samples():
+    """(hologram sha256, {view: (j, i, oracle field)}) from the stored samples."""
+    path = os.path.join(HERE, "golden", "uwa16k_mm_views_samples.txt")
+    dig = None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# hologram sha256"):
+                dig = line.split()[-1]
+    rows = np.loadtxt(path)
+    out = {}
+    for v in np.unique(rows[:, 0]).astype(int):
+        r = rows[rows[:, 0] == v]
+        out[v] = (r[:, 1].astype(np.int64), r[:, 2].astype(np.int64), r[:, 3] + 1j * r[:, 4])
+    return dig, out
+
+
+def test_uwa16k_mm_partial_views_vs_oracle_samples(nf):
+    """The benchmark's 16 partial views (FP32 path, one plan, the views one
+    after another on the loaded hologram) match the oracle within 1e-5 on
+    each view's samples, and each view's brightest oracle pixel is the GPU's."""
+    import synth
+    g = _mm_views_module()
+    W = g.W
+    dig, samples = read_mm_view_samples()
+    d_h = synth.gpu_hologram(W.point_cloud(), W.wavelength, W.pitch, W.n, W.n)
+    assert g.digest(d_h.cpu().numpy()) == dig, "the input generator made a different hologram"
+    plan = nf.Plan(W.wavelength, W.pitch, W.n, W.n, d_h)
+    del d_h
+    worst = 0.0
+    for v, kw in enumerate(g.views()):
+        view = nf.View(z=kw["z"], center_x=kw["cx"], center_y=kw["cy"], width=kw["w"],
+                       height=kw["h"], out_nx=kw["ox"], out_ny=kw["oy"], kind=nf.OUT_FIELD)
+        f = plan.reconstruct(view)
+        torch.cuda.synchronize()
+        f = f.cpu().numpy()
+        j, i, ref = samples[v]
+        got = f[j, i].astype(np.complex128)
+        e = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        worst = max(worst, e)
+        print("view %2d: sampled rel_l2 = %.3e" % (v, e))
+        assert e <= TOL, (v, e)
+        assert np.unravel_index(int(np.argmax(np.abs(f))), f.shape) == (j[-1], i[-1])
+    plan.close()
+    print("worst view: %.3e" % worst)
