@@ -257,6 +257,66 @@ def cufft_comparison(d_holo, info, stages, reps=3):
             "shapes": {"hologram": [ny, nx], "view": [npx, npy]}}
 
 
+def precision_vs_oracle(w, d_holo, nf):
+    """The workload's seeded partial views in each storage precision against the
+    FP64 oracle's samples (tests/golden/uwa16k_mm_views_samples.txt, written by
+    the oracle on the same generated hologram): relative L2 of the field and
+    intensity PSNR over the sampled pixels, worst view and all views pooled."""
+    import hashlib
+    import numpy as np
+    import torch
+    path = os.path.join(ROOT, "tests", "golden", "uwa16k_mm_views_samples.txt")
+    if not os.path.exists(path):
+        return {"error": "no oracle samples for this workload"}
+    dig = None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# hologram sha256"):
+                dig = line.split()[-1]
+    h = hashlib.sha256(np.ascontiguousarray(d_holo.cpu().numpy()).view(np.uint8)).hexdigest()
+    if h != dig:
+        return {"error": "hologram differs from the one the oracle samples were taken on"}
+    rows = np.loadtxt(path)
+    full = nf.view_plan(w.wavelength, w.pitch, w.n, w.n, nf.View(z=w.z_view))
+    p = full["pitch_out_x_m"]
+    s = w.partial_size
+    res = {"samples": int(rows.shape[0]), "views": w.partial_views,
+           "what": "field rel. L2 and intensity PSNR (peak = the samples' largest oracle "
+                   "intensity) over each view's sampled pixels against the FP64 oracle"}
+    for name, prec in (("fp32", nf.FP32), ("fp16_store", nf.FP16_STORE),
+                       ("bf16_store", nf.BF16_STORE)):
+        plan = nf.Plan(w.wavelength, w.pitch, w.n, w.n, d_holo, precision=prec)
+        got_all, ref_all, worst, worst_psnr = [], [], 0.0, float("inf")
+        for v, (dx, dy) in enumerate(w.partial_view_offsets()):
+            view = nf.View(z=w.z_view, center_x=float(dx) * p, center_y=float(dy) * p,
+                           width=s * p, height=s * p, out_nx=s, out_ny=s, kind=nf.OUT_FIELD)
+            f = plan.reconstruct(view)
+            torch.cuda.synchronize()
+            r = rows[rows[:, 0] == v]
+            j, i = r[:, 1].astype(np.int64), r[:, 2].astype(np.int64)
+            ref = r[:, 3] + 1j * r[:, 4]
+            got = f[torch.from_numpy(j).cuda(), torch.from_numpy(i).cuda()].cpu().numpy()
+            got = got.astype(np.complex128)
+            e = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            ir, ig = np.abs(ref) ** 2, np.abs(got) ** 2
+            mse = float(np.mean((ig - ir) ** 2))
+            ps = 10 * math.log10(float(ir.max()) ** 2 / mse) if mse > 0 else float("inf")
+            worst, worst_psnr = max(worst, e), min(worst_psnr, ps)
+            got_all.append(got)
+            ref_all.append(ref)
+            del f
+        plan.close()
+        g, r = np.concatenate(got_all), np.concatenate(ref_all)
+        ir, ig = np.abs(r) ** 2, np.abs(g) ** 2
+        mse = float(np.mean((ig - ir) ** 2))
+        res[name] = {"field_rel_l2_worst_view": float("%.3e" % worst),
+                     "field_rel_l2_all": float("%.3e" % (np.linalg.norm(g - r) / np.linalg.norm(r))),
+                     "intensity_psnr_db_worst_view": round(worst_psnr, 2),
+                     "intensity_psnr_db_all": round(10 * math.log10(float(ir.max()) ** 2 / mse), 2)
+                     if mse > 0 else None}
+    return res
+
+
 def cpu_baseline(w, min_seconds=10.0, n=1024):
     """The FP64 oracle as it stands on the host cores: full-view reconstruction
     of an n x n hologram of the workload's geometry (its central crop), repeated
@@ -508,6 +568,12 @@ def run_ours(args, w):
         vp.close()
         del vout
     line["precision_variants"] = variants
+    if w.name == "pointcloud-16384-532nm-0.307um-20000pt-z2-10mm":
+        try:
+            line["precision_vs_oracle"] = precision_vs_oracle(w, d_holo, nf)
+        except RuntimeError as e:
+            torch.cuda.empty_cache()
+            line["precision_vs_oracle"] = {"error": str(e).splitlines()[0][:200]}
     # the paper's polynomial surrogate for 2F1 (Section 4): plan initialisation
     # time (its purpose in the paper), step time, distance from the exact path
     t0 = time.time()

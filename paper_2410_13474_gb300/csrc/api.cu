@@ -261,7 +261,9 @@ static int plan_view_impl(const Geom *P, const nufds_view *v, ViewPlan *o) {
     long wx = o->khi_x - o->klo_x + 1, wy = o->khi_y - o->klo_y + 1;
     long npx = nice_size(wx > (long)chx ? wx : (long)chx);
     long npy = nice_size(wy > (long)chy ? wy : (long)chy);
-    if (npx > 24576 || npy > 24576) return NUFDS_EUNSUPPORTED;  // one row per CTA in smem
+    // rows up to kMaxRowL in one CTA's shared memory, up to twice that over a
+    // 2-CTA cluster
+    if (npx > 2 * kMaxRowL || npy > 2 * kMaxRowL) return NUFDS_EUNSUPPORTED;
     o->npx = (int)npx;
     o->npy = (int)npy;
     o->kc_x = (long)floor(0.5 * (double)(o->klo_x + o->khi_x));
@@ -1206,6 +1208,14 @@ static int batch_impl(nufds_plan *const *plans, const nufds_view *views, void *c
             rc = NUFDS_EUNSUPPORTED;
         if (!rc) rc = fft_plan_get(b.V.npx, &b.fpx);
         if (!rc) rc = fft_plan_get(b.V.npy, &b.fpy);
+        if (!rc && (b.fpx->split != 1 || b.fpy->split != 1)) {
+            // rows split over a CTA pair have single-view kernels only: such a
+            // view runs on its own, on the batch's stream, in its batch order
+            rc = reconstruct_impl(P, &views[i], outs[i], st);
+            if (rc) fail(i, rc);
+            else if (statuses) statuses[i] = NUFDS_OK;
+            continue;
+        }
         if (rc) {
             fail(i, rc);
             continue;

@@ -29,6 +29,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 
 namespace nufds {
@@ -264,16 +266,18 @@ __device__ __forceinline__ void fused_mid_r(const PassArgs &P, float2 *sm,
     }
 }
 
-// the odd half: reload the chirped samples, modulate, first forward DIT pass
+// the odd half: reload the chirped samples, modulate (mod: per slot, group-major),
+// first forward DIT pass
 template <int R>
 __device__ __forceinline__ void odd_first_r(const PassArgs &P, float2 *sm,
-                                            const float2 *__restrict__ scr) {
+                                            const float2 *__restrict__ scr,
+                                            const float2 *__restrict__ mod) {
     const int ng = P.L / R;
     for (int g = threadIdx.x; g < ng; g += blockDim.x) {
         const int base = g * R;
         float2 x[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) x[i] = cmul(scr[i * ng + g], __ldg(P.mod1_slot + i * ng + g));
+        for (int i = 0; i < R; ++i) x[i] = cmul(scr[i * ng + g], __ldg(mod + i * ng + g));
         Dft<R, false>::run(x);
 #pragma unroll
         for (int k = 0; k < R; ++k) sm[phys(base + k)] = x[k];
@@ -453,7 +457,7 @@ __device__ __forceinline__ void row_view_body(const PassArgs &P, const T *__rest
 #undef C_
     __syncthreads();
     forward_tail<T>(P, sm, tws, orow, sc, 0);
-#define C_(R) odd_first_r<R>(P, sm, scr)
+#define C_(R) odd_first_r<R>(P, sm, scr, P.mod1_slot)
     NUFDS_RADIX_SWITCH(RL, C_)
 #undef C_
     __syncthreads();
@@ -510,6 +514,148 @@ __global__ void __launch_bounds__(512) k_rows_view_batch(const PassArgs *__restr
         row_view_body<T>(sP, (const T *)I.in + (long)r * I.in_ld, (T *)I.out + (long)r * I.out_ld,
                          I.chirp, scr, sm, tws, inv, sc);
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------
+// Split rows: one view-pass row over a cluster of two CTAs (rows longer than
+// one CTA's shared memory holds).  With L the row length and L/2 the length
+// each CTA transforms:
+//   inverse: X[2k + c] = sum_{n < L/2} (x[n] + (-1)^c x[n + L/2]) W^{-cn}_L W^{-nk}_{L/2},
+//            so CTA c folds the row on the way in (radix-2 step, pass 0 of
+//            the decimation in frequency) and holds the odd or even outputs;
+//   chirp:   pointwise (natural index 2k + c of its slots);
+//   forward: X[k] = Z_0[k mod L/2] + W^k_L Z_1[k mod L/2], Z_c the half-length
+//            DFT of CTA c's samples (times the odd-half modulation): each CTA
+//            leaves Z_c in natural order in shared memory and computes its
+//            half of the outputs from both, reading its partner's through
+//            distributed shared memory (radix-2 step, pass 0 of the
+//            decimation in time).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float2 twl_at(const float2 *twl, int n) {  // W_L^n, n < L/2
+    return cmul(twl[64 + (n >> 6)], twl[n & 63]);
+}
+
+template <int R, class TI>
+__device__ __forceinline__ void dif_first_split_r(const PassArgs &P, const TI *__restrict__ irow,
+                                                  float inv, float2 *sm, const float2 *tws,
+                                                  const float2 *twl, int c) {
+    const int s = P.stride[0], Lh = P.L;
+    for (int o = threadIdx.x; o < s; o += blockDim.x) {
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int n = o + i * s;
+            const float2 x0 = ld_cs(irow, n, inv), x1 = ld_cs(irow, n + Lh, inv);
+            x[i] = c ? cmulc(csub(x0, x1), twl_at(twl, n)) : cadd(x0, x1);
+        }
+        Dft<R, true>::run(x);
+        if (o) {
+            float2 W[R];
+            tw_powers<R>(tw_base(tws, o), W);
+#pragma unroll
+            for (int k = 1; k < R; ++k) x[k] = twmul<true>(x[k], W[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) sm[phys(o + k * s)] = x[k];
+    }
+}
+
+// last forward DIT pass kept in shared memory: natural-order outputs
+template <int R>
+__device__ __forceinline__ void dit_last_smem_r(const PassArgs &P, float2 *sm, const float2 *tws) {
+    const int s = P.stride[0];
+    for (int o = threadIdx.x; o < s; o += blockDim.x) {
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = sm[phys(o + i * s)];
+        if (o) {
+            float2 W[R];
+            tw_powers<R>(tw_base(tws, o), W);
+#pragma unroll
+            for (int i = 1; i < R; ++i) x[i] = twmul<false>(x[i], W[i]);
+        }
+        Dft<R, false>::run(x);
+#pragma unroll
+        for (int k = 0; k < R; ++k) sm[phys(o + k * s)] = x[k];
+    }
+}
+
+__device__ void forward_tail_smem(const PassArgs &P, float2 *sm, const float2 *tws) {
+    for (int j = P.npass - 2; j >= 1; --j) {
+        mid_pass<false, true>(P, j, sm, tws);
+        __syncthreads();
+    }
+#define C_(R) dit_last_smem_r<R>(P, sm, tws)
+    NUFDS_RADIX_SWITCH(P.radix[0], C_)
+#undef C_
+}
+
+// outputs k = c L/2 + k' of half a: (-1)^k (Z_0[k'] + W_L^k Z_1[k']), W_L^{L/2} = -1,
+// stored in the plane layout at a L + k
+template <class TO>
+__device__ __forceinline__ void split_combine(const PassArgs &P, const float2 *sm,
+                                              const float2 *peer, const float2 *twl, int c,
+                                              TO *__restrict__ orow, float sc, int a) {
+    const int Lh = P.L;
+    for (int k = threadIdx.x; k < Lh; k += blockDim.x) {
+        const float2 zo = sm[phys(k)], zp = peer[phys(k)];
+        const float2 z0 = c ? zp : zo, z1 = c ? zo : zp;
+        float2 t = cmul(z1, twl_at(twl, k));
+        if (c) t = make_float2(-t.x, -t.y);
+        float2 v = cadd(z0, t);
+        const int f = c * Lh + k;
+        if (f & 1) v = make_float2(-v.x, -v.y);
+        st_cs(orow, (long)a * P.Lfull + f, v, sc);
+    }
+}
+
+template <class T>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
+    k_rows_view_split(PassArgs P, const T *__restrict__ in, long in_ld,
+                      const float2 *__restrict__ chirp_slot, T *__restrict__ out, long out_ld,
+                      int rows, float2 *__restrict__ scratch, const float *sc_in,
+                      const float *sc_out) {
+    extern __shared__ float2 sm[];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)cl.block_rank();
+    const float2 *peer = cl.map_shared_rank(sm, c ^ 1);
+    const float2 *tws = load_tw(P, sm);
+    float2 *twl = sm + phys(P.L) + 1 + 64 + P.ncoarse;
+    for (int i = threadIdx.x; i < 64 + (P.L + 63) / 64; i += blockDim.x) twl[i] = P.twL[i];
+    __syncthreads();
+    const float inv = sc_in ? 1.0f / *sc_in : 1.0f, sc = sc_out ? *sc_out : 1.0f;
+    float2 *scr = scratch + (long)blockIdx.x * P.L;
+    const float2 *chirp = chirp_slot + (long)c * P.L, *mod = P.mod1_slot + (long)c * P.L;
+    const int RL = P.radix[P.npass - 1];
+    for (int r = blockIdx.x >> 1; r < rows; r += gridDim.x >> 1) {
+        const T *irow = in + (long)r * in_ld;
+        T *orow = out + (long)r * out_ld;
+#define C_(R) dif_first_split_r<R, T>(P, irow, inv, sm, tws, twl, c)
+        NUFDS_RADIX_SWITCH(P.radix[0], C_)
+#undef C_
+        __syncthreads();
+        for (int j = 1; j < P.npass - 1; ++j) {
+            mid_pass<true, false>(P, j, sm, tws);
+            __syncthreads();
+        }
+#define C_(R) fused_mid_r<R>(P, sm, chirp, scr)
+        NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
+        __syncthreads();
+        forward_tail_smem(P, sm, tws);
+        cl.sync();
+        split_combine<T>(P, sm, peer, twl, c, orow, sc, 0);
+        cl.sync();
+#define C_(R) odd_first_r<R>(P, sm, scr, mod)
+        NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
+        __syncthreads();
+        forward_tail_smem(P, sm, tws);
+        cl.sync();
+        split_combine<T>(P, sm, peer, twl, c, orow, sc, 1);
+        cl.sync();
     }
 }
 
@@ -695,30 +841,38 @@ static int init_constants() {
     return 0;
 }
 
-static int slot_to_index(const FftPlan &p, int slot) {
-    int n = 0;
-    for (int j = 0; j < p.npass; ++j) n += ((slot / p.stride[j]) % p.radix[j]) * p.prefix[j];
-    return n;
-}
-
 // Plan of length L and its host tables:
-//   f2: fine[64] | coarse[ncoarse] | mod1[L] | mod1_slot[L]; dea[L]; pad[L]
+//   f2: fine[64] | coarse[ncoarse] | mod1[L] | mod1_slot[L] [| twL fine[64] | twL coarse[ncl]];
+//   dea[L]; pad[L]
+// (for a split row the twiddles fine/coarse are those of the half length, and
+// twL holds W_L^n, n < L/2, for the radix-2 steps between the halves)
+static int split_ncoarse(int L) { return fft_needs_split(L) ? (L / 2 + 63) / 64 : 0; }
+
 static int plan_host(int L, FftPlan &p, std::vector<float2> &f2, std::vector<double> &dea,
                      std::vector<float> &pad) {
-    if (L < 64 || (L % 4) || !choose_radices(L, p)) return -3;
-    int t = (L / 16 + 31) / 32 * 32;
+    if (L < 64 || (L % 4)) return -3;
+    const int split = fft_needs_split(L) ? 2 : 1, Lh = L / split;
+    if ((Lh % 4) || Lh < 64 || !choose_radices(Lh, p)) return -3;
+    p.L = L;
+    p.split = split;
+    int t = (Lh / 16 + 31) / 32 * 32;
     p.threads = t < 64 ? 64 : (t > 512 ? 512 : t);
     p.pad_threads = p.threads;
-    p.ncoarse = (L + 63) / 64;
-    p.smem_bytes = sizeof(float2) * (size_t)(host_phys(L) + 1 + 64 + p.ncoarse);
+    p.ncoarse = (Lh + 63) / 64;
+    const int ncl = split_ncoarse(L);
+    p.smem_bytes = sizeof(float2) * (size_t)(host_phys(Lh) + 1 + 64 + p.ncoarse +
+                                             (split == 2 ? 64 + ncl : 0));
     if (p.smem_bytes > 227 * 1024 - 1024) return -3;
-    f2.assign(64 + p.ncoarse + 2 * (size_t)L, make_float2(0.f, 0.f));
+    // a split row whose halves fit two CTAs per SM: blocks small enough that
+    // two of them also fit the register file
+    if (split == 2 && 2 * (p.smem_bytes + 1024) <= 227 * 1024) p.threads = p.pad_threads = 256;
+    f2.assign(fft_tw_count(L), make_float2(0.f, 0.f));
     for (int j = 0; j < 64; ++j) {
-        double a = -2.0 * M_PI * j / L;
+        double a = -2.0 * M_PI * j / Lh;
         f2[j] = make_float2((float)cos(a), (float)sin(a));
     }
     for (int i = 0; i < p.ncoarse; ++i) {
-        double a = -2.0 * M_PI * (double)(64L * i % L) / L;
+        double a = -2.0 * M_PI * (double)(64L * i % Lh) / Lh;
         f2[64 + i] = make_float2((float)cos(a), (float)sin(a));
     }
     float2 *mod1 = f2.data() + 64 + p.ncoarse, *mod1s = mod1 + L;
@@ -726,7 +880,18 @@ static int plan_host(int L, FftPlan &p, std::vector<float2> &f2, std::vector<dou
         double a = -M_PI * (n - L / 2) / (double)L;
         mod1[n] = make_float2((float)cos(a), (float)sin(a));
     }
-    for (int q = 0; q < L; ++q) mod1s[fft_gm_pos(p, q)] = mod1[slot_to_index(p, q)];
+    for (int q = 0; q < L; ++q) mod1s[fft_gm_pos(p, q)] = mod1[fft_index_of_slot(p, q)];
+    if (split == 2) {
+        float2 *tl = mod1s + L;
+        for (int j = 0; j < 64; ++j) {
+            double a = -2.0 * M_PI * j / L;
+            tl[j] = make_float2((float)cos(a), (float)sin(a));
+        }
+        for (int i = 0; i < ncl; ++i) {
+            double a = -2.0 * M_PI * (double)(64L * i) / L;
+            tl[64 + i] = make_float2((float)cos(a), (float)sin(a));
+        }
+    }
     std::vector<double> ft;
     es_fourier(L, ft);
     dea.resize(L);
@@ -744,6 +909,7 @@ static void plan_point(FftPlan &p, const float2 *tw, const double *dea, const fl
     p.tw = tw;
     p.mod1 = tw + 64 + p.ncoarse;
     p.mod1_slot = p.mod1 + p.L;
+    p.twL = p.split == 2 ? p.mod1_slot + p.L : nullptr;
     p.deapod = dea;
     p.pad_pre = pad;
 }
@@ -868,7 +1034,7 @@ int fft_plan_get(int L, const FftPlan **out) {
     cudaMemcpy(e->pad_pre, pad.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
     plan_point(e->plan, e->dev, e->deapod, e->pad_pre);
     set_smem_attrs(e->plan.smem_bytes);
-    autotune_threads(e->plan);
+    if (e->plan.split == 1) autotune_threads(e->plan);  // split rows: the default block size
     g_cache[key] = e;
     *out = &e->plan;
     return 0;
@@ -903,12 +1069,17 @@ int fft_plan_fill(int L, FftPlan *p, float2 *d_tw, double *d_deapod, float *d_pa
     return 0;
 }
 
-size_t fft_tw_count(int L) { return 64 + (size_t)(L + 63) / 64 + 2 * (size_t)L; }
+size_t fft_tw_count(int L) {
+    const int ncl = split_ncoarse(L), Lh = ncl ? L / 2 : L;
+    return 64 + (size_t)(Lh + 63) / 64 + 2 * (size_t)L + (ncl ? 64 + (size_t)ncl : 0);
+}
 
 PassArgs fft_pass_args(const FftPlan &p) {
     PassArgs a;
     memset(&a, 0, sizeof a);
-    a.L = p.L;
+    a.L = p.L / p.split;
+    a.Lfull = p.L;
+    a.twL = p.twL;
     a.npass = p.npass;
     a.ncoarse = p.ncoarse;
     for (int j = 0; j < p.npass; ++j) {
@@ -939,6 +1110,9 @@ static void set_smem_attrs(size_t bytes) {
         cudaFuncSetAttribute(k_rows_view_batch<float2>, a, m);
         cudaFuncSetAttribute(k_rows_view_batch<__half2>, a, m);
         cudaFuncSetAttribute(k_rows_view_batch<__nv_bfloat162>, a, m);
+        cudaFuncSetAttribute(k_rows_view_split<float2>, a, m);
+        cudaFuncSetAttribute(k_rows_view_split<__half2>, a, m);
+        cudaFuncSetAttribute(k_rows_view_split<__nv_bfloat162>, a, m);
     }
 }
 
@@ -953,7 +1127,16 @@ static int grid_for(const void *fn, const FftPlan &p, int rows) {
 }
 
 int rows_view_grid(const FftPlan &p, int rows) {
-    return grid_for((const void *)k_rows_view<float2>, p, rows);
+    if (p.split == 1) return grid_for((const void *)k_rows_view<float2>, p, rows);
+    // two CTAs per row: an even grid of at most the resident CTAs
+    int dev, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k_rows_view_split<float2>,
+                                                  p.threads, p.smem_bytes);
+    long g = (long)sms * (per < 1 ? 1 : per);
+    g = std::min(g, 2L * rows);
+    return (int)std::max(2L, g & ~1L);
 }
 
 int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, void *out,
@@ -961,6 +1144,7 @@ int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, 
                      cudaStream_t st, int natural_out, const float *pre, float2 *pair_scr,
                      size_t pair_cap) {
     if (rows <= 0) return 0;
+    if (p.split != 1) return -3;  // hologram rows are at most kMaxRowL long
     FftPlan q = p;
     q.threads = p.pad_threads;
     const int grid = grid_for((const void *)k_rows_pad2<float2, float2>, q, rows);
@@ -989,6 +1173,20 @@ int launch_rows_view(const FftPlan &p, const void *in, long in_ld, const float2 
                      const float *sc_in, const float *sc_out, cudaStream_t st) {
     if (rows <= 0) return 0;
     const PassArgs a = fft_pass_args(p);
+    if (p.split == 2) {
+        if (grid & 1) return -3;
+#define L_(T)                                                                              \
+    k_rows_view_split<T><<<grid, p.threads, p.smem_bytes, st>>>(a, (const T *)in, in_ld,   \
+                                                               chirp, (T *)out, out_ld,    \
+                                                               rows, scratch, sc_in, sc_out)
+        if (prec == PREC_F32) L_(float2);
+        else if (prec == PREC_F16) L_(__half2);
+        else if (prec == PREC_BF16) L_(__nv_bfloat162);
+        else return -3;
+#undef L_
+        count_launch();
+        return check_launch();
+    }
 #define L_(T)                                                                               \
     k_rows_view<T><<<grid, p.threads, p.smem_bytes, st>>>(a, (const T *)in, in_ld, chirp,   \
                                                          (T *)out, out_ld, rows, scratch,   \

@@ -71,8 +71,18 @@ constexpr int16_t kMasked = -32768;
 // ---------------------------------------------------------------------------
 constexpr int kMaxPasses = 8;
 
+// Rows longer than kMaxRowL points do not fit one CTA's shared memory; such a
+// row is split over a cluster of two CTAs (split = 2): a radix-2 step on the
+// way in (inverse) and out (forward), a half-length transform of L / 2 points
+// in each CTA, and the halves exchanged through distributed shared memory.
+// The pass structure (npass, radix, stride, prefix, ncoarse, tw) is then that
+// of the half-length transform; L, deapod, pad_pre and mod1 stay full length.
+constexpr int kMaxRowL = 24576;
+inline bool fft_needs_split(int L) { return L > kMaxRowL; }
+
 struct FftPlan {
     int L = 0;
+    int split = 1;                     // 2: the row is split over a 2-CTA cluster
     int npass = 0;
     int radix[kMaxPasses] = {};
     int stride[kMaxPasses] = {};   // s_j = L / (r_1 ... r_j)
@@ -88,10 +98,11 @@ struct FftPlan {
     const float2 *mod1_slot = nullptr; // the same per slot, group-major order (fft_gm_pos)
     const double *deapod = nullptr;    // 1 / psi_hat(n - L/2)
     const float *pad_pre = nullptr;    // (-1)^n / psi_hat(n - L/2)
+    const float2 *twL = nullptr;       // split rows: W_L^j (j < 64) | W_L^{64 i} (i < ncoarse)
 };
 
 struct PassArgs {
-    int L, npass, ncoarse;
+    int L, npass, ncoarse;            // of the (half-length, for split rows) transform
     int radix[kMaxPasses], stride[kMaxPasses];
     uint32_t mag_stride[kMaxPasses];  // ceil(2^32 / stride), 0 for stride 1
     uint32_t mag_radix[kMaxPasses];   // ceil(2^32 / radix)
@@ -100,6 +111,8 @@ struct PassArgs {
     const float *pad_pre;             // (-1)^n / psi_hat(n - L/2), natural order
     int natural_out;                  // padded output: 0 plane-wise (a L + k), 1 natural (2k + a),
                                       // 2 natural, stored in pairs through a scratch row
+    int Lfull;                        // row length (2 L for split rows)
+    const float2 *twL;                // split rows: W_Lfull fine | coarse, as tw
 };
 
 // kernel arguments of plan p
@@ -128,20 +141,22 @@ int rows_view_batch_grid(int threads, size_t smem, int total_rows);
 int launch_transpose_batch(const TrItem *d_items, const int *d_tile_off, int nitems,
                            int total_tiles, int prec, cudaStream_t st);
 
-// Natural index of a digit-reversed slot of plan p (host and device).
+// Natural index of a digit-reversed slot of plan p (host and device).  For a
+// split row, slot c L/2 + q is slot q of half c, which holds index 2 n_q + c.
 __host__ __device__ inline int fft_index_of_slot(const FftPlan &p, int slot) {
+    const int Lh = p.L / p.split, c = slot / Lh, q = slot - c * Lh;
     int n = 0;
-    for (int j = 0; j < p.npass; ++j) n += ((slot / p.stride[j]) % p.radix[j]) * p.prefix[j];
-    return n;
+    for (int j = 0; j < p.npass; ++j) n += ((q / p.stride[j]) % p.radix[j]) * p.prefix[j];
+    return p.split * n + c;
 }
 // Position of digit-reversed slot q in the group-major order of the last
 // pass (radix R, L / R groups): element k of group g (slot g R + k) at
 // k (L / R) + g, so that lanes handling consecutive groups touch
 // consecutive addresses.  The per-slot tables (chirp, odd-half modulation)
 // and the odd-half scratch are kept in this order.
-__host__ __device__ inline int fft_gm_pos(const FftPlan &p, int q) {
-    const int R = p.radix[p.npass - 1];
-    return (q % R) * (p.L / R) + q / R;
+__host__ __device__ inline int fft_gm_pos(const FftPlan &p, int slot) {
+    const int R = p.radix[p.npass - 1], Lh = p.L / p.split, c = slot / Lh, q = slot - c * Lh;
+    return c * Lh + (q % R) * (Lh / R) + q / R;
 }
 // float2 count of the twiddle/modulation table of length L
 size_t fft_tw_count(int L);

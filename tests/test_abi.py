@@ -153,14 +153,18 @@ def test_plain_frt_planner_matches_oracle(built):
 
 
 def test_planner_limits(built):
-    """Largest supported FFT: N' <= 24576 per axis (one row per CTA in shared
-    memory); a plain-FrT full view of a 16K hologram needs more and is
+    """Largest supported FFT: N' <= 49152 per axis (rows up to 24576 in one
+    CTA's shared memory, longer ones split over a 2-CTA cluster): the
+    plain-FrT full view of a 16K hologram at 120 deg needs 36864 and is
+    planned; a 16K view at 0.5 mm needs ~95000 by the chirp rule and is
     refused; nx must be a positive multiple of 4."""
     lam, pitch = 532e-9, 0.307e-6
     ok = nf.view_plan(lam, pitch, 16384, 16384, nf.View(z=0.8))
-    assert ok["np_x"] <= 24576
+    assert ok["np_x"] == 23040
+    plain = nf.view_plan(lam, pitch, 16384, 16384, nf.View(z=0.8, mode=nf.MODE_PLAIN_FRT))
+    assert plain["np_x"] == plain["np_y"] == 36864
     with pytest.raises(nf.NufdsError) as e:
-        nf.view_plan(lam, pitch, 16384, 16384, nf.View(z=0.8, mode=nf.MODE_PLAIN_FRT))
+        nf.view_plan(lam, pitch, 16384, 16384, nf.View(z=0.5e-3))
     assert e.value.code == nf.EUNSUPPORTED
     with pytest.raises(nf.NufdsError) as e:
         nf.view_plan(lam, pitch, 64, 64, nf.View(z=0.5, out_nx=70000, out_ny=8))
