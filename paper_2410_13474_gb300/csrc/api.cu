@@ -445,6 +445,38 @@ struct Sweep {
     }
 };
 
+// The part of a view's arrays its passes need (the partial view processes
+// its spectral sub-band, Section 4): S is zero outside the band's rows
+// [bx0, bx1) (x) and columns [by0, by1) (y), so the stretch and the y pass run
+// on the band rows only and both passes read the band columns only; the remap
+// reads only the fine rows of Q within a window of the band's y extent,
+// [m0, m1), which sit in plane a at rows a npy + [k0[a], k1[a]), so the
+// transpose and the x pass produce only those (all rows when a window would
+// wrap around the periodic grid).
+struct BandWork {
+    int bx0, bx1, by0, by1;
+    int k0[2], k1[2];
+    int rows_x() const { return (k1[0] - k0[0]) + (k1[1] - k0[1]); }
+};
+static BandWork band_work(const ViewPlan &V) {
+    BandWork b;
+    b.bx0 = (int)std::max(0L, V.klo_x - V.kc_x + V.npx / 2);
+    b.bx1 = (int)std::min((long)V.npx, V.khi_x - V.kc_x + V.npx / 2 + 1);
+    b.by0 = (int)std::max(0L, V.klo_y - V.kc_y + V.npy / 2);
+    b.by1 = (int)std::min((long)V.npy, V.khi_y - V.kc_y + V.npy / 2 + 1);
+    long m0 = 2 * (V.klo_y - V.kc_y) + V.npy - kW / 2 - 2;
+    long m1 = 2 * (V.khi_y - V.kc_y) + V.npy + kW / 2 + 3;
+    if (m0 < 0 || m1 > 2L * V.npy) {
+        m0 = 0;
+        m1 = 2L * V.npy;
+    }
+    for (int a = 0; a < 2; ++a) {  // plane a holds fine rows 2k + a at row a npy + k
+        b.k0[a] = (int)((m0 - a + 1) / 2);
+        b.k1[a] = (int)((m1 - a + 1) / 2);
+    }
+    return b;
+}
+
 static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cudaStream_t st,
                             Sweep *sw = nullptr) {
     if (!P || !v || !d_out) return NUFDS_EINVAL;
@@ -511,6 +543,12 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
              })))
             return rc;
     }
+    // work only where the view needs it (band_work)
+    const BandWork bw = band_work(V);
+    const int bx0 = bw.bx0, bx1 = bw.bx1, by0 = bw.by0, by1 = bw.by1;
+    const int *k0 = bw.k0, *k1 = bw.k1;
+    const int nbr = bx1 - bx0, nqr = bw.rows_x();
+    const size_t ebv = prec_bytes(P->prec);
     // step two: stretch gather -> S_T in Bf (npx x npy)
     StretchArgs sa = {};
     sa.G = P->G;
@@ -530,6 +568,8 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     sa.kc_y = V.kc_y;
     sa.npx = V.npx;
     sa.npy = V.npy;
+    sa.jx0 = bx0;
+    sa.jn = nbr;
     sa.S = S;
     sa.plain = V.plain;
     sa.linear = P->linear;
@@ -542,7 +582,8 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     // algorithmic bytes of the gather: table entries of the band, the part of
     // G the band pulls back to (in proportion to the full band), S written
     const double g_frac = (nbx * nby) / ((double)P->pb_nkx * P->pb_nky);
-    const double st_bytes = 12.0 * nbx * nby + 32.0 * q * P->nx * P->ny * g_frac + 8.0 * q * np2;
+    const double st_bytes =
+        12.0 * nbx * nby + 32.0 * q * P->nx * P->ny * g_frac + 8.0 * q * nbr * V.npy;
     if (!(sw && sw->same(V))) {  // a sweep reuses the band of an earlier depth
         if (P->prec == NUFDS_FP16_STORE &&
             cudaMemsetAsync(P->acc + kEnergyAcc, 0, kEnergySlots * sizeof(double), st) !=
@@ -558,21 +599,40 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
             return rc;
         if (sw) sw->set(V);
     }
-    // steps two/three along y: S_T rows (npx of npy) -> A (npx x 2npy)
-    if ((rc = stage(P, ST_VIEW_ROWS_Y, 24.0 * q * np2, st, [&] {
-             return launch_rows_view(*fpy, S, V.npy, chy, A, 2 * V.npy, V.npx, scr, W.grid_y,
-                                     P->prec, scale_ptr(P, 2), scale_ptr(P, 3), st);
+    (void)np2;
+    // steps two/three along y: S_T band rows (of npy, read in [by0, by1)) -> A (npx x 2npy)
+    if ((rc = stage(P, ST_VIEW_ROWS_Y, 8.0 * q * nbr * (by1 - by0) + 16.0 * q * nbr * V.npy, st,
+                    [&] {
+             return launch_rows_view(*fpy, (const char *)S + ebv * bx0 * V.npy, V.npy, chy,
+                                     (char *)A + ebv * bx0 * 2 * V.npy, 2 * V.npy, nbr, scr,
+                                     rows_view_grid(*fpy, nbr), P->prec, scale_ptr(P, 2),
+                                     scale_ptr(P, 3), st, by0, by1);
          })))
         return rc;
-    // A (npx x 2npy) -> Bf (2npy x npx)
-    if ((rc = stage(P, ST_VIEW_TRANSPOSE, 32.0 * q * np2, st, [&] {
-             return launch_transpose(A, 2 * V.npy, Bf, V.npx, V.npx, 2 * V.npy, P->prec, st);
+    // A (band rows x the needed fine rows) -> Bf (needed fine rows x band columns)
+    if ((rc = stage(P, ST_VIEW_TRANSPOSE, 16.0 * q * nbr * nqr, st, [&] {
+             int r = 0;
+             for (int a = 0; a < 2 && !r; ++a)
+                 if (k1[a] > k0[a])
+                     r = launch_transpose(
+                         (const char *)A + ebv * ((size_t)bx0 * 2 * V.npy + (size_t)a * V.npy + k0[a]),
+                         2 * V.npy, (char *)Bf + ebv * (((size_t)a * V.npy + k0[a]) * V.npx + bx0),
+                         V.npx, nbr, k1[a] - k0[a], P->prec, st);
+             return r;
          })))
         return rc;
-    // along x: Bf rows (2npy of npx) -> A = Q (2npy x 2npx)
-    if ((rc = stage(P, ST_VIEW_ROWS_X, 48.0 * q * np2, st, [&] {
-             return launch_rows_view(*fpx, Bf, V.npx, chx, A, 2 * V.npx, 2 * V.npy, scr,
-                                     W.grid_x, P->prec, scale_ptr(P, 4), scale_ptr(P, 5), st);
+    // along x: the needed rows of Bf (read in [bx0, bx1)) -> those rows of A = Q (2npy x 2npx)
+    if ((rc = stage(P, ST_VIEW_ROWS_X, 8.0 * q * nqr * nbr + 16.0 * q * nqr * V.npx, st, [&] {
+             int r = 0;
+             for (int a = 0; a < 2 && !r; ++a)
+                 if (k1[a] > k0[a]) {
+                     const size_t row = (size_t)a * V.npy + k0[a];
+                     r = launch_rows_view(*fpx, (const char *)Bf + ebv * row * V.npx, V.npx, chx,
+                                          (char *)A + ebv * row * 2 * V.npx, 2 * V.npx,
+                                          k1[a] - k0[a], scr, rows_view_grid(*fpx, k1[a] - k0[a]),
+                                          P->prec, scale_ptr(P, 4), scale_ptr(P, 5), st, bx0, bx1);
+                 }
+             return r;
          })))
         return rc;
     // step five: remap
@@ -807,18 +867,34 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         int first = 0, count = 0, rows = 0, threads = 64, maxL = 0, grid = 0;
         size_t smem = 0;
     };
+    // Row items: the y pass one per view on its band rows, the x pass one per
+    // view and plane of the rows of Q its remap reads (band_work)
+    struct Slot {
+        int view, plane, rows;
+        const FftPlan *f;
+    };
+    std::vector<BandWork> bws(n);
+    std::vector<Slot> slots[2];
+    for (int i = 0; i < n; ++i) {
+        const BandWork &bw = bws[i] = band_work(w[i].V);
+        slots[0].push_back({i, -1, bw.bx1 - bw.bx0, w[i].fpy});
+        for (int a = 0; a < 2; ++a)
+            if (bw.k1[a] > bw.k0[a]) slots[1].push_back({i, a, bw.k1[a] - bw.k0[a], w[i].fpx});
+    }
+    const int nri = (int)(slots[0].size() + slots[1].size()), ntr = (int)slots[1].size();
     RowClass cls[2][kRowClasses];
-    std::vector<int> order[2];  // view indices of the y and x items, by class
+    std::vector<int> order[2];  // slot indices of the y and x items, by class
     for (int pass = 0; pass < 2; ++pass) {
         for (int c = 0; c < kRowClasses; ++c) {
             RowClass &rc = cls[pass][c];
             rc.first = (int)order[pass].size();
-            for (int i = 0; i < n; ++i) {
-                const FftPlan *f = pass == 0 ? w[i].fpy : w[i].fpx;
+            for (size_t q = 0; q < slots[pass].size(); ++q) {
+                const Slot &sl = slots[pass][q];
+                const FftPlan *f = sl.f;
                 if (row_class(f) != c) continue;
-                order[pass].push_back(i);
+                order[pass].push_back((int)q);
                 rc.count++;
-                rc.rows += pass == 0 ? w[i].V.npx : 2 * w[i].V.npy;
+                rc.rows += sl.rows;
                 rc.threads = std::max(rc.threads, std::min(512, f->threads));
                 rc.maxL = std::max(rc.maxL, f->L);
                 rc.smem = std::max(rc.smem, f->smem_bytes);
@@ -835,9 +911,9 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
     // descriptors: PassArgs[], RowItem[2n], row offsets, TrItem[n], tile offsets,
     // StretchArgs[n], RemapArgs[n], offsets
     const size_t desc_bytes = align256(sizeof(PassArgs) * fps.size()) +
-                              align256(sizeof(RowItem) * 2 * n) +
-                              align256(sizeof(int) * 2 * (n + kRowClasses)) +
-                              align256(sizeof(TrItem) * n) + align256(sizeof(int) * (n + 1)) +
+                              align256(sizeof(RowItem) * nri) +
+                              align256(sizeof(int) * (nri + 2 * kRowClasses)) +
+                              align256(sizeof(TrItem) * ntr) + align256(sizeof(int) * (ntr + 1)) +
                               align256(sizeof(StretchArgs) * n) + align256(sizeof(int) * (n + 1)) +
                               align256(sizeof(RemapArgs) * n) + align256(sizeof(int) * (n + 1)) +
                               align256(sizeof(ChirpItem) * 2 * n) + align256(sizeof(int) * (2 * n + 1));
@@ -885,10 +961,10 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
     // ---- descriptors (host), mirrored at ddesc
     size_t o = 0;
     auto carve = [&](size_t bytes) { size_t r = o; o += align256(bytes); return r; };
-    const size_t o_pa = carve(sizeof(PassArgs) * fps.size()), o_ri = carve(sizeof(RowItem) * 2 * n),
-                 o_roff = carve(sizeof(int) * 2 * (n + kRowClasses)),
-                 o_tr = carve(sizeof(TrItem) * n),
-                 o_toff = carve(sizeof(int) * (n + 1)), o_sa = carve(sizeof(StretchArgs) * n),
+    const size_t o_pa = carve(sizeof(PassArgs) * fps.size()), o_ri = carve(sizeof(RowItem) * nri),
+                 o_roff = carve(sizeof(int) * (nri + 2 * kRowClasses)),
+                 o_tr = carve(sizeof(TrItem) * ntr),
+                 o_toff = carve(sizeof(int) * (ntr + 1)), o_sa = carve(sizeof(StretchArgs) * n),
                  o_soff = carve(sizeof(int) * (n + 1)), o_ra = carve(sizeof(RemapArgs) * n),
                  o_roff2 = carve(sizeof(int) * (n + 1)), o_ch = carve(sizeof(ChirpItem) * 2 * n),
                  o_choff = carve(sizeof(int) * (2 * n + 1));
@@ -918,8 +994,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         int nbx, nby;
     };
     std::vector<Regions> R(n);
-    std::vector<RowItem> items_y(n), items_x(n);
-    int ttr = 0, tst = 0, trm = 0;
+    std::vector<const float *> scSv(n), scTv(n), scQv(n);
+    int ttr = 0, tst = 0, trm = 0, itr = 0;
     for (int i = 0; i < n; ++i) {
         BatchView &b = w[i];
         const ViewPlan &V = b.V;
@@ -990,6 +1066,8 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         sa.kc_y = V.kc_y;
         sa.npx = V.npx;
         sa.npy = V.npy;
+        sa.jx0 = bws[i].bx0;
+        sa.jn = bws[i].bx1 - bws[i].bx0;
         sa.S = g.Bf;
         sa.plain = V.plain;
         sa.prec = prec;
@@ -997,35 +1075,25 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         sa.sc_s = scS;
         sa.energy = prec == NUFDS_FP16_STORE ? g.acc + kEnergyAcc : nullptr;
         hsoff[i] = tst;
-        tst += stretch_tiles(V.npx, V.npy);
-        RowItem &ry = items_y[i];
-        ry.in = g.Bf;
-        ry.out = g.A;
-        ry.chirp = g.chy;
-        ry.in_ld = V.npy;
-        ry.out_ld = 2 * V.npy;
-        ry.args = fidx(b.fpy);
-        ry.sc_in = scS;
-        ry.sc_out = scT;
-        RowItem &rx = items_x[i];
-        rx.in = g.Bf;
-        rx.out = g.A;
-        rx.chirp = g.chx;
-        rx.in_ld = V.npx;
-        rx.out_ld = 2 * V.npx;
-        rx.args = fidx(b.fpx);
-        rx.sc_in = scT;
-        rx.sc_out = scQ;
-        TrItem &tr = htr[i];
-        tr.in = g.A;
-        tr.out = g.Bf;
-        tr.in_ld = 2 * V.npy;
-        tr.out_ld = V.npx;
-        tr.rows = V.npx;
-        tr.cols = 2 * V.npy;
-        tr.tiles_x = (tr.cols + 31) / 32;
-        htoff[i] = ttr;
-        ttr += tr.tiles_x * ((tr.rows + 31) / 32);
+        tst += stretch_tiles(sa.jn, V.npy);
+        scSv[i] = scS;
+        scTv[i] = scT;
+        scQv[i] = scQ;
+        // the band rows of A by the needed columns (fine rows of Q), per plane
+        const BandWork &bw = bws[i];
+        for (int a = 0; a < 2; ++a) {
+            if (bw.k1[a] <= bw.k0[a]) continue;
+            TrItem &tr = htr[itr];
+            tr.in = (char *)g.A + eb * ((size_t)bw.bx0 * 2 * V.npy + (size_t)a * V.npy + bw.k0[a]);
+            tr.out = (char *)g.Bf + eb * (((size_t)a * V.npy + bw.k0[a]) * V.npx + bw.bx0);
+            tr.in_ld = 2 * V.npy;
+            tr.out_ld = V.npx;
+            tr.rows = bw.bx1 - bw.bx0;
+            tr.cols = bw.k1[a] - bw.k0[a];
+            tr.tiles_x = (tr.cols + 31) / 32;
+            htoff[itr++] = ttr;
+            ttr += tr.tiles_x * ((tr.rows + 31) / 32);
+        }
         RemapArgs &ra = hra[i];
         ra.Q = g.A;
         ra.npx = V.npx;
@@ -1062,16 +1130,46 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
                 coff[pass][c] = hroff + off;
                 int rows = 0;
                 for (int q = 0; q < rc.count; ++q) {
-                    const int i = order[pass][rc.first + q];
-                    hri[k++] = pass == 0 ? items_y[i] : items_x[i];
+                    const Slot &sl = slots[pass][order[pass][rc.first + q]];
+                    const int i = sl.view;
+                    const ViewPlan &V = w[i].V;
+                    const BandWork &bw = bws[i];
+                    const Regions &g = R[i];
+                    RowItem it;
+                    memset(&it, 0, sizeof it);
+                    if (pass == 0) {  // S band rows (read in [by0, by1)) -> A
+                        it.in = (char *)g.Bf + eb * (size_t)bw.bx0 * V.npy;
+                        it.out = (char *)g.A + eb * (size_t)bw.bx0 * 2 * V.npy;
+                        it.chirp = g.chy;
+                        it.in_ld = V.npy;
+                        it.out_ld = 2 * V.npy;
+                        it.args = fidx(w[i].fpy);
+                        it.sc_in = scSv[i];
+                        it.sc_out = scTv[i];
+                        it.in_lo = bw.by0;
+                        it.in_hi = bw.by1;
+                    } else {  // the needed rows of one plane (read in [bx0, bx1)) -> Q
+                        const size_t row = (size_t)sl.plane * V.npy + bw.k0[sl.plane];
+                        it.in = (char *)g.Bf + eb * row * V.npx;
+                        it.out = (char *)g.A + eb * row * 2 * V.npx;
+                        it.chirp = g.chx;
+                        it.in_ld = V.npx;
+                        it.out_ld = 2 * V.npx;
+                        it.args = fidx(w[i].fpx);
+                        it.sc_in = scTv[i];
+                        it.sc_out = scQv[i];
+                        it.in_lo = bw.bx0;
+                        it.in_hi = bw.bx1;
+                    }
+                    hri[k++] = it;
                     hroff[off++] = rows;
-                    rows += pass == 0 ? w[i].V.npx : 2 * w[i].V.npy;
+                    rows += sl.rows;
                 }
                 hroff[off++] = rows;
             }
         }
     }
-    htoff[n] = ttr;
+    htoff[ntr] = ttr;
     hchoff[2 * n] = tch;
     hsoff[n] = tst;
     hrmoff[n] = trm;
@@ -1134,7 +1232,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         for (int i = 0; i < n && !rc && prec == NUFDS_FP16_STORE; ++i)
             rc = launch_scales_view(R[i].sc, R[i].acc, w[i].fpx->dmax, w[i].fpy->dmax, st);
         auto rows_pass = [&](int pass) {
-            int r = 0, item0 = pass == 0 ? 0 : n;
+            int r = 0, item0 = pass == 0 ? 0 : (int)slots[0].size();
             for (int c = 0; c < kRowClasses && !r; ++c) {
                 const RowClass &k = cls[pass][c];
                 if (!k.count) continue;
@@ -1148,7 +1246,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         if (!rc && (where = "rows_y")) rc = rows_pass(0);
         if (!rc && (where = "transpose"))
             rc = launch_transpose_batch((const TrItem *)(ddesc + o_tr),
-                                        (const int *)(ddesc + o_toff), n, ttr, prec, st);
+                                        (const int *)(ddesc + o_toff), ntr, ttr, prec, st);
         if (!rc && (where = "rows_x")) rc = rows_pass(1);
         if (!rc && (where = "remap"))
             rc = launch_remap_batch((const RemapArgs *)(ddesc + o_ra),

@@ -221,14 +221,19 @@ __device__ __forceinline__ void mid_pass_r(const PassArgs &P, int j, float2 *sm,
 }
 
 // pass 0 of the inverse DIF, reading the natural-order row from global memory
+// (elements outside [lo, hi) are zero and not read)
 template <int R, class TI>
 __device__ __forceinline__ void dif_first_r(const PassArgs &P, const TI *__restrict__ irow,
-                                            float inv, float2 *sm, const float2 *tws) {
+                                            float inv, float2 *sm, const float2 *tws, int lo,
+                                            int hi) {
     const int s = P.stride[0];
     for (int o = threadIdx.x; o < s; o += blockDim.x) {
         float2 x[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) x[i] = ld_cs(irow, o + i * s, inv);
+        for (int i = 0; i < R; ++i) {
+            const int n = o + i * s;
+            x[i] = n >= lo && n < hi ? ld_cs(irow, n, inv) : make_float2(0.f, 0.f);
+        }
         Dft<R, true>::run(x);
         if (o) {
             float2 W[R];
@@ -435,15 +440,17 @@ __global__ void __launch_bounds__(512) k_rows_pad2(PassArgs P, const TI *__restr
 }
 
 // one row of the view pass: inverse DFT, chirp, the two half-grid forward DFTs
+// (input elements outside [lo, hi) are zero)
 template <class T>
 __device__ __forceinline__ void row_view_body(const PassArgs &P, const T *__restrict__ irow,
                                               T *__restrict__ orow,
                                               const float2 *__restrict__ chirp_slot,
                                               float2 *__restrict__ scr, float2 *sm,
-                                              const float2 *tws, float inv, float sc) {
+                                              const float2 *tws, float inv, float sc, int lo,
+                                              int hi) {
     const int RL = P.radix[P.npass - 1];
     // inverse DFT (DIF): natural -> slot order
-#define C_(R) dif_first_r<R, T>(P, irow, inv, sm, tws)
+#define C_(R) dif_first_r<R, T>(P, irow, inv, sm, tws, lo, hi)
     NUFDS_RADIX_SWITCH(P.radix[0], C_)
 #undef C_
     __syncthreads();
@@ -470,14 +477,15 @@ __global__ void __launch_bounds__(512) k_rows_view(PassArgs P, const T *__restri
                                                    const float2 *__restrict__ chirp_slot,
                                                    T *__restrict__ out, long out_ld, int rows,
                                                    float2 *__restrict__ scratch,
-                                                   const float *sc_in, const float *sc_out) {
+                                                   const float *sc_in, const float *sc_out,
+                                                   int lo, int hi) {
     extern __shared__ float2 sm[];
     const float2 *tws = load_tw(P, sm);
     const float inv = sc_in ? 1.0f / *sc_in : 1.0f, sc = sc_out ? *sc_out : 1.0f;
     float2 *scr = scratch + (long)blockIdx.x * P.L;
     for (int r = blockIdx.x; r < rows; r += gridDim.x)
         row_view_body<T>(P, in + (long)r * in_ld, out + (long)r * out_ld, chirp_slot, scr, sm, tws,
-                         inv, sc);
+                         inv, sc, lo, hi);
 }
 
 // Batched view pass over rows of many items (views, passes) of uneven length:
@@ -512,7 +520,7 @@ __global__ void __launch_bounds__(512) k_rows_view_batch(const PassArgs *__restr
         }
         const int r = g - row_off[it];
         row_view_body<T>(sP, (const T *)I.in + (long)r * I.in_ld, (T *)I.out + (long)r * I.out_ld,
-                         I.chirp, scr, sm, tws, inv, sc);
+                         I.chirp, scr, sm, tws, inv, sc, I.in_lo, I.in_hi);
         __syncthreads();
     }
 }
@@ -539,14 +547,16 @@ __device__ __forceinline__ float2 twl_at(const float2 *twl, int n) {  // W_L^n, 
 template <int R, class TI>
 __device__ __forceinline__ void dif_first_split_r(const PassArgs &P, const TI *__restrict__ irow,
                                                   float inv, float2 *sm, const float2 *tws,
-                                                  const float2 *twl, int c) {
+                                                  const float2 *twl, int c, int lo, int hi) {
     const int s = P.stride[0], Lh = P.L;
+    const float2 zero = make_float2(0.f, 0.f);
     for (int o = threadIdx.x; o < s; o += blockDim.x) {
         float2 x[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const int n = o + i * s;
-            const float2 x0 = ld_cs(irow, n, inv), x1 = ld_cs(irow, n + Lh, inv);
+            const float2 x0 = n >= lo && n < hi ? ld_cs(irow, n, inv) : zero;
+            const float2 x1 = n + Lh >= lo && n + Lh < hi ? ld_cs(irow, n + Lh, inv) : zero;
             x[i] = c ? cmulc(csub(x0, x1), twl_at(twl, n)) : cadd(x0, x1);
         }
         Dft<R, true>::run(x);
@@ -615,7 +625,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
     k_rows_view_split(PassArgs P, const T *__restrict__ in, long in_ld,
                       const float2 *__restrict__ chirp_slot, T *__restrict__ out, long out_ld,
                       int rows, float2 *__restrict__ scratch, const float *sc_in,
-                      const float *sc_out) {
+                      const float *sc_out, int lo, int hi) {
     extern __shared__ float2 sm[];
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -632,7 +642,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
     for (int r = blockIdx.x >> 1; r < rows; r += gridDim.x >> 1) {
         const T *irow = in + (long)r * in_ld;
         T *orow = out + (long)r * out_ld;
-#define C_(R) dif_first_split_r<R, T>(P, irow, inv, sm, tws, twl, c)
+#define C_(R) dif_first_split_r<R, T>(P, irow, inv, sm, tws, twl, c, lo, hi)
         NUFDS_RADIX_SWITCH(P.radix[0], C_)
 #undef C_
         __syncthreads();
@@ -969,7 +979,7 @@ static void autotune_threads(FftPlan &p) {
                     if (rep == 1) cudaEventRecord(e0, st);
                     if (kind == 0)
                         k_rows_view<float2><<<grid, t, p.smem_bytes, st>>>(
-                            a, in, L, chirp, out, 2 * L, rows, scr, nullptr, nullptr);
+                            a, in, L, chirp, out, 2 * L, rows, scr, nullptr, nullptr, 0, L);
                     else
                         k_rows_pad2<float2, float2><<<grid, t, p.smem_bytes, st>>>(
                             a, in, L, out, 2 * L, rows, nullptr, nullptr, nullptr);
@@ -1170,15 +1180,19 @@ int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, 
 
 int launch_rows_view(const FftPlan &p, const void *in, long in_ld, const float2 *chirp, void *out,
                      long out_ld, int rows, float2 *scratch, int grid, int prec,
-                     const float *sc_in, const float *sc_out, cudaStream_t st) {
+                     const float *sc_in, const float *sc_out, cudaStream_t st, int in_lo,
+                     int in_hi) {
     if (rows <= 0) return 0;
+    in_lo = std::max(in_lo, 0);
+    in_hi = std::min(in_hi, p.L);
     const PassArgs a = fft_pass_args(p);
     if (p.split == 2) {
         if (grid & 1) return -3;
 #define L_(T)                                                                              \
     k_rows_view_split<T><<<grid, p.threads, p.smem_bytes, st>>>(a, (const T *)in, in_ld,   \
                                                                chirp, (T *)out, out_ld,    \
-                                                               rows, scratch, sc_in, sc_out)
+                                                               rows, scratch, sc_in, sc_out, \
+                                                               in_lo, in_hi)
         if (prec == PREC_F32) L_(float2);
         else if (prec == PREC_F16) L_(__half2);
         else if (prec == PREC_BF16) L_(__nv_bfloat162);
@@ -1190,7 +1204,7 @@ int launch_rows_view(const FftPlan &p, const void *in, long in_ld, const float2 
 #define L_(T)                                                                               \
     k_rows_view<T><<<grid, p.threads, p.smem_bytes, st>>>(a, (const T *)in, in_ld, chirp,   \
                                                          (T *)out, out_ld, rows, scratch,   \
-                                                         sc_in, sc_out)
+                                                         sc_in, sc_out, in_lo, in_hi)
     if (prec == PREC_F32) L_(float2);
     else if (prec == PREC_F16) L_(__half2);
     else if (prec == PREC_BF16) L_(__nv_bfloat162);

@@ -285,8 +285,8 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
     // a warp covers 32 consecutive band points along y (measured faster than
     // 8 x 4 blocks, whose lanes' windows spread over more lines of G)
     const int jy = bx * 32 + threadIdx.x;
-    const int jx = by * 8 + threadIdx.y;
-    const bool inside = jx < a.npx && jy < a.npy;
+    const int jx = a.jx0 + by * 8 + threadIdx.y;
+    const bool inside = jx - a.jx0 < (a.jn ? a.jn : a.npx) && jx < a.npx && jy < a.npy;
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
     bool valid = false;
     short2 b = make_short2(0, 0);
@@ -489,8 +489,8 @@ __device__ __forceinline__ float2 lerp2(const float2 *__restrict__ A, long ld, i
 
 // step two: S(f'_k) = bilinear of the unpadded spectrum at the pulled-back f
 __global__ void __launch_bounds__(256) k_stretch_linear(StretchArgs a) {
-    const int jy = blockIdx.x * 32 + threadIdx.x, jx = blockIdx.y * 8 + threadIdx.y;
-    if (jx >= a.npx || jy >= a.npy) return;
+    const int jy = blockIdx.x * 32 + threadIdx.x, jx = a.jx0 + blockIdx.y * 8 + threadIdx.y;
+    if (jx - a.jx0 >= (a.jn ? a.jn : a.npx) || jx >= a.npx || jy >= a.npy) return;
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
     float2 acc = make_float2(0.f, 0.f);
     bool valid = false;
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(256, 4) k_remap_batch(const RemapArgs *__restr
 
 int launch_stretch(const StretchArgs &a, cudaStream_t st) {
     if (es_init()) return -4;
-    dim3 grid((a.npy + 31) / 32, (a.npx + 7) / 8);
+    dim3 grid((a.npy + 31) / 32, ((a.jn ? a.jn : a.npx) + 7) / 8);
     if (a.linear && a.prec != PREC_F32) return -3;
     if (a.linear) k_stretch_linear<<<grid, dim3(32, 8), 0, st>>>(a);
     else if (a.prec == PREC_F32) k_stretch<float2><<<grid, dim3(32, 8), 0, st>>>(a);

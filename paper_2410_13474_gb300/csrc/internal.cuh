@@ -127,6 +127,7 @@ struct RowItem {
     long in_ld, out_ld;
     int args;               // index into the PassArgs array
     const float *sc_in, *sc_out;
+    int in_lo, in_hi;       // input elements outside [in_lo, in_hi) are zero (not read)
 };
 struct TrItem {
     const void *in;
@@ -186,10 +187,12 @@ int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, 
 // View pass: rows of length L: inverse centred DFT (input already carries
 // (-1)^k), multiply by chirp[n] (complex, includes deapodisation and 1/L),
 // then the padded forward pass as above (output 2L per row).  scratch holds
-// grid-size * L float2.
+// grid-size * L float2.  Input elements outside [in_lo, in_hi) are taken as
+// zero and not read (the band of a view whose spectrum is zero elsewhere).
 int launch_rows_view(const FftPlan &p, const void *in, long in_ld, const float2 *chirp, void *out,
                      long out_ld, int rows, float2 *scratch, int grid, int prec,
-                     const float *sc_in, const float *sc_out, cudaStream_t st);
+                     const float *sc_in, const float *sc_out, cudaStream_t st, int in_lo = 0,
+                     int in_hi = 1 << 30);
 int rows_view_grid(const FftPlan &p, int rows);
 
 // out[c][r] = in[r][c]
@@ -274,6 +277,7 @@ struct StretchArgs {
     int pb_nkx, pb_nky;
     long klo_x, khi_x, klo_y, khi_y, kc_x, kc_y;
     int npx, npy;
+    int jx0, jn;            // rows jx0 .. jx0 + jn - 1 of S are computed (jn = 0: all npx)
     // G's fine columns (y) in natural order, rows (x) plane-wise
     void *S;                // output, layout [jx][jy], npx x npy
     int prec;               // storage of G and S
@@ -288,7 +292,7 @@ int launch_stretch(const StretchArgs &a, cudaStream_t st);
 // batched: item i owns blocks [off[i], off[i+1]) of a 1-D grid (32 x 8 tiles)
 int launch_stretch_batch(const StretchArgs *d_items, const int *d_off, int nitems, int total,
                          int prec, cudaStream_t st);
-inline int stretch_tiles(int npx, int npy) { return ((npy + 31) / 32) * ((npx + 7) / 8); }
+inline int stretch_tiles(int rows, int npy) { return ((npy + 31) / 32) * ((rows + 7) / 8); }
 
 struct RemapArgs {
     const void *Q;          // oversampled FrT output, layout [my][mx], 2npy x 2npx

@@ -90,3 +90,36 @@ def test_batch_mixed_precisions(nf):
     assert np.array_equal(o16.cpu().numpy(), r16)
     pl32.close()
     pl16.close()
+
+
+def test_batch_views_match_oracle(nf):
+    """A mixed batch (three holograms, full and partial views, on and off the
+    full view's lattice, field and intensity) against the FP64 oracle view by
+    view: field within 1e-5, intensity within 3e-5 (relative L2)."""
+    import oracle
+    specs = [(128, 532e-9, 0.4e-6, 0.6e-3), (256, 532e-9, 0.35e-6, 0.8e-3), (192, 640e-9, 0.5e-6, 1e-3)]
+    plans, views, outs, cases = [], [], [], []
+    for i, (n, lam, pitch, z) in enumerate(specs):
+        rng = np.random.default_rng(40 + i)
+        H = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+        pl = nf.Plan(lam, pitch, n, n, torch.from_numpy(H).cuda())
+        for v in _views(nf, pl, z, 40 + i)[1:5]:
+            plans.append(pl)
+            views.append(v)
+            outs.append(pl.output_like(v))
+            cases.append((H, lam, pitch, v))
+    st = nf.reconstruct_batch(plans, views, outs)
+    torch.cuda.synchronize()
+    assert all(s == 0 for s in st), st
+    worst = 0.0
+    for o, (H, lam, pitch, v) in zip(outs, cases):
+        f, I = oracle.reconstruct(H, lam, pitch, v.z, v.center_x, v.center_y, v.width, v.height,
+                                  v.out_nx, v.out_ny)
+        got = o.cpu().numpy()
+        ref = f if v.kind == nf.OUT_FIELD else I
+        e = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        worst = max(worst, e)
+        assert e <= (1e-5 if v.kind == nf.OUT_FIELD else 3e-5), (v, e)
+    print("batch vs oracle: worst rel_l2 %.3e over %d views" % (worst, len(outs)))
+    for p in {id(p): p for p in plans}.values():
+        p.close()

@@ -1,6 +1,7 @@
 """Serving on the GPU: requests arriving while others run are batched and
 overlap on two streams; every result must equal the same view reconstructed
-alone (bitwise: batching does not change the per-element arithmetic)."""
+alone (bitwise: batching does not change the per-element arithmetic), and a
+subset of the served results matches the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -17,10 +18,11 @@ def test_served_results_equal_alone():
     from paper_2410_13474_gb300.serving import GpuExecutor, Request, Scheduler
 
     specs = [(128, 0.4e-6, 0.6e-3), (256, 0.35e-6, 0.9e-3), (192, 0.45e-6, 1.2e-3)]
-    plans = []
+    plans, holos = [], []
     rng = np.random.default_rng(5)
     for n, pitch, _ in specs:
         h = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+        holos.append(h)
         plans.append(nf.Plan(532e-9, pitch, n, n, torch.from_numpy(h).cuda()))
     reqs = []
     for i in range(48):
@@ -42,5 +44,16 @@ def test_served_results_equal_alone():
         assert r.status == 0
         alone = plans[r.holo].reconstruct(r.view)
         assert torch.equal(alone, r.out), r.rid
+    # and a subset against the FP64 oracle
+    import oracle
+    for r in reqs[::6]:
+        n, pitch, _ = specs[r.holo]
+        v = r.view
+        f, I = oracle.reconstruct(holos[r.holo], 532e-9, pitch, v.z, v.center_x, v.center_y,
+                                  v.width, v.height, v.out_nx, v.out_ny)
+        ref = f if v.kind == nf.OUT_FIELD else I
+        got = r.out.cpu().numpy()
+        e = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        assert e <= (1e-5 if v.kind == nf.OUT_FIELD else 3e-5), (r.rid, e)
     for p in plans:
         p.close()
