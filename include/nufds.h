@@ -90,7 +90,7 @@ extern "C" {
 #define NUFDS_MODE_NUFDS 0     /* the NU-FDS method (stretch, FrT, Eq. 17 remap)          */
 #define NUFDS_MODE_PLAIN_FRT 1 /* Eq. 2 alone at z: no stretch, x' = x_o (the paper's Fig.
                                 * 10b comparison).  Band from the view's own extent; views
-                                * needing N' > 24576 are NUFDS_EUNSUPPORTED; not available
+                                * needing N' > 49152 are NUFDS_EUNSUPPORTED; not available
                                 * in nufds_reconstruct_noalloc */
 
 typedef struct nufds_plan nufds_plan;
@@ -98,8 +98,8 @@ typedef struct nufds_plan nufds_plan;
 typedef struct nufds_params {
     double wavelength_m;       /* lambda > 0, lambda < 2 pitch (Eq. 1)                  */
     double pitch_m;            /* hologram pixel pitch Delta                            */
-    int32_t nx, ny;            /* hologram size; multiple of 4, 64 <= n <= 16384 (else
-                                * NUFDS_EUNSUPPORTED)                                    */
+    int32_t nx, ny;            /* hologram size; 5-smooth, 64 <= n <= 32768, a multiple
+                                * of 4 (of 8 above 24576) (else NUFDS_EUNSUPPORTED)      */
     int32_t precision;         /* NUFDS_FP32, NUFDS_FP16_STORE or NUFDS_BF16_STORE      */
     int32_t flags;             /* 0, or NUFDS_FLAG_PAPER_POLY_M and/or _PAPER_LINEAR   */
     uint64_t hbm_budget_bytes; /* cap on device memory the plan may allocate; 0 = none  */
@@ -164,8 +164,10 @@ int nufds_view_plan(const nufds_params *params, const nufds_view *view, nufds_vi
  * Reconstruct one view of the loaded hologram into d_out (out_ny x out_nx,
  * float32 intensity or complex64 field).  Asynchronous on cuda_stream.  The
  * plan's workspace grows on first use of a larger view (that call allocates
- * and synchronises).  Views whose band leaves the full-view band are
- * NUFDS_EUNSUPPORTED.
+ * and synchronises).  Calls on different streams may use one plan: each
+ * waits, on its stream, for the previous call's use of the plan's workspace.
+ * Views whose band leaves the full-view band, or that need N' > 49152 on an
+ * axis, are NUFDS_EUNSUPPORTED (rows of N' > 24576 run split over two CTAs).
  */
 int nufds_reconstruct(nufds_plan *plan, const nufds_view *view, void *d_out, void *cuda_stream);
 
@@ -176,7 +178,9 @@ int nufds_reconstruct(nufds_plan *plan, const nufds_view *view, void *d_out, voi
  * runs as one CUDA graph: per-view tables, then one persistent launch per
  * stage over all views.  Results are bitwise those of nufds_reconstruct.
  * The batch workspace is kept per (device, stream), so batches on different
- * streams may run concurrently (their plans' spectra are only read).
+ * streams may run concurrently (their plans' spectra are only read).  Views
+ * with N' > 24576 on an axis run one by one as nufds_reconstruct, on
+ * cuda_stream, in batch order.
  * statuses (may be NULL) receives one code per view; a failing view does not
  * stop the others (views of a plan created with NUFDS_FLAG_PAPER_LINEAR get
  * NUFDS_EUNSUPPORTED).  Returns NUFDS_OK if every view succeeded, else the

@@ -91,7 +91,7 @@ struct nufds_plan {
     short2 *pb_base = nullptr;
     float2 *pb_frac = nullptr;
     // output map on the full-view pixel lattice (z independent)
-    short2 *rm_base = nullptr;
+    int2 *rm_base = nullptr;
     uint2 *rm_frac = nullptr;
     nufds::GeomTables *tab = nullptr;  // owner of the four tables above (shared)
     // cached oversampled spectrum, [mx][my], in the plan's storage precision
@@ -118,6 +118,10 @@ struct nufds_plan {
     };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> events;
+    // the workspace's last user: calls on another stream wait for it (two
+    // streams may drive one plan, e.g. serving slots)
+    cudaEvent_t ws_ev = nullptr;
+    cudaStream_t ws_stream = nullptr;
 };
 
 namespace nufds {
@@ -334,12 +338,27 @@ static int view_ws(const nufds_plan *P, const ViewPlan &V, const FftPlan *fpx, c
     w->nbx = (int)(2 * (V.khi_x - V.klo_x) + 17);
     w->nby = (int)(2 * (V.khi_y - V.klo_y) + 17);
     w->outc = kind == NUFDS_OUT_FIELD_C64 ? align256(sizeof(OutChirp) * (w->nbx + w->nby)) : 0;
-    w->rm = V.lattice ? 0 : align256((sizeof(short2) + sizeof(uint2)) * (size_t)V.ox * V.oy + 256);
+    w->rm = V.lattice ? 0 : align256((sizeof(int2) + sizeof(uint2)) * (size_t)V.ox * V.oy + 256);
     // a focal sweep keeps the stretched band (S_T) apart from B, which the
     // Fresnel passes of each depth overwrite
     w->keep = keep_band ? align256(eb * np) : 0;
     w->total = w->A + w->B + w->scr + w->chirp + w->outc + w->rm + w->keep;
     (void)P;
+    return NUFDS_OK;
+}
+
+// Order uses of the plan's workspace across streams: wait for the last user
+// (when it was another stream), and mark this stream as the last user.
+static int ws_acquire(nufds_plan *P, cudaStream_t st) {
+    if (P->ws_ev && P->ws_stream != st && cudaStreamWaitEvent(st, P->ws_ev, 0) != cudaSuccess)
+        return NUFDS_ECUDA;
+    return NUFDS_OK;
+}
+static int ws_release(nufds_plan *P, cudaStream_t st) {
+    if (!P->ws_ev && cudaEventCreateWithFlags(&P->ws_ev, cudaEventDisableTiming) != cudaSuccess)
+        return NUFDS_ECUDA;
+    if (cudaEventRecord(P->ws_ev, st) != cudaSuccess) return NUFDS_ECUDA;
+    P->ws_stream = st;
     return NUFDS_OK;
 }
 
@@ -382,7 +401,7 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
     const size_t eb = prec_bytes(P->prec);
     const size_t half = align256(eb * 2 * (size_t)P->nx * P->ny);
     int rc = ensure_ws(P, 2 * half);
-    if (rc) return rc;
+    if (rc || (rc = ws_acquire(P, st))) return rc;
     void *A = P->ws, *Bf = P->ws + half;
     const float2 *H = (const float2 *)d_holo;
     const double n2 = (double)P->nx * P->ny, q = eb / 8.0;
@@ -415,7 +434,7 @@ static int load_impl(nufds_plan *P, const void *d_holo, cudaStream_t st) {
          })))
         return rc;
     P->loaded = true;
-    return NUFDS_OK;
+    return ws_release(P, st);
 }
 
 // Stretched band kept across the views of a focal sweep: the pull-back and
@@ -495,7 +514,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ViewWs W;
     view_ws(P, V, fpx, fpy, v->out_kind, &W, sw != nullptr);
     if (sw && W.total > P->ws_bytes) sw->valid = false;  // the workspace moves
-    if ((rc = ensure_ws(P, W.total))) return rc;
+    if ((rc = ensure_ws(P, W.total)) || (rc = ws_acquire(P, st))) return rc;
     char *p = P->ws;
     void *A = p;
     p += W.A;
@@ -509,7 +528,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     p += W.keep;
     OutChirp *Ex = (OutChirp *)p, *Ey = Ex + W.nbx;
     p += W.outc;
-    short2 *rmb = P->rm_base;
+    int2 *rmb = P->rm_base;
     uint2 *rmf = P->rm_frac;
     long rm_ld = P->nx, rm_i0 = 0, rm_j0 = 0;
     if (V.lattice) {
@@ -517,9 +536,9 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
         rm_j0 = V.j0;
     } else {
         rmf = (uint2 *)p;
-        rmb = (short2 *)(p + align256(sizeof(uint2) * (size_t)V.ox * V.oy));
+        rmb = (int2 *)(p + align256(sizeof(uint2) * (size_t)V.ox * V.oy));
         rm_ld = V.ox;
-        if ((rc = stage(P, ST_TABLES, 12.0 * V.ox * V.oy, st, [&] {
+        if ((rc = stage(P, ST_TABLES, 16.0 * V.ox * V.oy, st, [&] {
                  return launch_remap_table(P->lam, P->pitch, P->nx, P->ny, V.z, V.cx, V.cy, V.px,
                                            V.py, V.ox, V.oy, rmb, rmf, st, V.plain, P->geom.mf);
              })))
@@ -576,7 +595,6 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     sa.prec = P->prec;
     sa.sc_g = scale_ptr(P, 1);
     sa.sc_s = scale_ptr(P, 2);
-    sa.energy = P->prec == NUFDS_FP16_STORE ? P->acc + kEnergyAcc : nullptr;
     const double np2 = (double)V.npx * V.npy, q = prec_bytes(P->prec) / 8.0;
     const double nbx = (double)(V.khi_x - V.klo_x + 1), nby = (double)(V.khi_y - V.klo_y + 1);
     // algorithmic bytes of the gather: table entries of the band, the part of
@@ -585,16 +603,14 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     const double st_bytes =
         12.0 * nbx * nby + 32.0 * q * P->nx * P->ny * g_frac + 8.0 * q * nbr * V.npy;
     if (!(sw && sw->same(V))) {  // a sweep reuses the band of an earlier depth
-        if (P->prec == NUFDS_FP16_STORE &&
-            cudaMemsetAsync(P->acc + kEnergyAcc, 0, kEnergySlots * sizeof(double), st) !=
-                cudaSuccess)
-            return NUFDS_ECUDA;
         if ((rc = stage(P, ST_STRETCH, st_bytes, st, [&] { return launch_stretch(sa, st); })))
             return rc;
-        // the FP16 scales of S and of the passes depend on S's energy only
+        // the FP16 scales of the passes depend on S's energy only (its band rows)
         if (P->prec == NUFDS_FP16_STORE &&
-            (rc = stage(P, ST_TABLES, 0.0, st, [&] {
-                 return launch_scales_view(P->sc, P->acc, fpx->dmax, fpy->dmax, st);
+            (rc = stage(P, ST_TABLES, 4.0 * nbr * V.npy, st, [&] {
+                 int r = launch_energy((const char *)S + ebv * bx0 * V.npy, (long)nbr * V.npy,
+                                       scale_ptr(P, 2), P->acc + kEnergyAcc, st);
+                 return r ? r : launch_scales_view(P->sc, P->acc, fpx->dmax, fpy->dmax, st);
              })))
             return rc;
         if (sw) sw->set(V);
@@ -661,9 +677,11 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ra.sc_q = scale_ptr(P, 5);
     ra.linear = P->linear;
     // Q region the view maps into, its table, the output
-    const double rm_bytes = 32.0 * q * nbx * nby + 12.0 * V.ox * V.oy +
+    const double rm_bytes = 32.0 * q * nbx * nby + 16.0 * V.ox * V.oy +
                             (v->out_kind == NUFDS_OUT_INTENSITY_F32 ? 4.0 : 8.0) * V.ox * V.oy;
-    return stage(P, ST_REMAP, rm_bytes, st, [&] { return launch_remap(ra, st); });
+    if ((rc = stage(P, ST_REMAP, rm_bytes, st, [&] { return launch_remap(ra, st); })))
+        return rc;
+    return ws_release(P, st);
 }
 
 // The FP64-derived tables of a geometry (pull-back on the full-view band,
@@ -676,7 +694,7 @@ struct GeomTables {
     double lam, pitch;
     short2 *pb_base = nullptr;
     float2 *pb_frac = nullptr;
-    short2 *rm_base = nullptr;
+    int2 *rm_base = nullptr;
     uint2 *rm_frac = nullptr;
     int refs = 0;
 };
@@ -721,7 +739,7 @@ static int tables_acquire(nufds_plan *P, int flags, cudaStream_t st) {
     const size_t npb = (size_t)P->pb_nkx * P->pb_nky, npix = (size_t)P->nx * P->ny;
     if (cudaMalloc(&t->pb_base, npb * sizeof(short2)) != cudaSuccess ||
         cudaMalloc(&t->pb_frac, npb * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&t->rm_base, npix * sizeof(short2)) != cudaSuccess ||
+        cudaMalloc(&t->rm_base, npix * sizeof(int2)) != cudaSuccess ||
         cudaMalloc(&t->rm_frac, npix * sizeof(uint2)) != cudaSuccess) {
         cudaGetLastError();
         tables_free(t);
@@ -731,21 +749,32 @@ static int tables_acquire(nufds_plan *P, int flags, cudaStream_t st) {
     // lattice (computed at z = 1, valid at every z)
     const double B1 = full_width(P->lam, P->pitch, 1.0);
     int rc;
+    // coarse pre-images seeding the table's Newton solves (freed below; the
+    // table is built without them if the allocation fails)
+    double2 *coarse = nullptr;
+    if (cudaMalloc(&coarse, sizeof(double2) * (size_t)pullback_coarse_count(P->pb_nkx, P->pb_nky)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        coarse = nullptr;
+    }
     if ((rc = launch_pullback_table(P->lam, P->pitch, P->nx, P->ny, P->pb_kx0, P->pb_nkx,
                                     P->pb_ky0, P->pb_nky, t->pb_base, t->pb_frac, st,
-                                    P->geom.mf)) ||
+                                    P->geom.mf, coarse)) ||
         (rc = launch_remap_table(P->lam, P->pitch, P->nx, P->ny, 1.0, 0.0, 0.0, B1 / P->nx,
                                  B1 / P->ny, P->nx, P->ny, t->rm_base, t->rm_frac, st, 0,
                                  P->geom.mf))) {
         cudaStreamSynchronize(st);
+        cudaFree(coarse);
         tables_free(t);
         return rc;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(coarse);
         tables_free(t);
         return NUFDS_ECUDA;
     }
+    cudaFree(coarse);
     t->refs = 1;
     g_tabs.push_back(t);
     P->tab = t;
@@ -760,11 +789,15 @@ static void free_plan(nufds_plan *P) {
     cudaFree(P->lin_pre);
     cudaFree(P->ws);
     for (cudaEvent_t e : P->events) cudaEventDestroy(e);
+    if (P->ws_ev) cudaEventDestroy(P->ws_ev);
     delete P;
 }
 
+// hologram sides: 64 .. 32768, 5-smooth, a multiple of 4 (of 8 above kMaxRowL,
+// whose rows split over two CTAs into halves that are multiples of 4)
 static bool fft_size_ok(int n) {
-    if (n < 64 || n > 16384 || n % 4) return false;  // row FFTs need L >= 64
+    if (n < 64 || n > 32768 || n % 4) return false;  // row FFTs need L >= 64
+    if (fft_needs_split(n) && n % 8) return false;
     int m = n;
     for (int p : {2, 3, 5})
         while (m % p == 0) m /= p;
@@ -820,7 +853,7 @@ static size_t view_batch_bytes(const BatchView &b, int prec) {
                align256(sizeof(float2) * (b.V.npx + b.V.npy)) + 256;
     if (b.kind == NUFDS_OUT_FIELD_C64)
         t += align256(sizeof(OutChirp) * (4 * (b.V.khi_x - b.V.klo_x) + 4 * (b.V.khi_y - b.V.klo_y) + 68));
-    if (!b.V.lattice) t += 2 * align256((sizeof(short2) + sizeof(uint2)) * (size_t)b.V.ox * b.V.oy);
+    if (!b.V.lattice) t += 2 * align256((sizeof(int2) + sizeof(uint2)) * (size_t)b.V.ox * b.V.oy);
     return t;
 }
 
@@ -986,7 +1019,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         void *A, *Bf;
         float2 *chx, *chy;
         OutChirp *Ex, *Ey;
-        short2 *rmb;
+        int2 *rmb;
         uint2 *rmf;
         float *sc;
         double *acc;
@@ -1031,7 +1064,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
             rm_j0 = V.j0;
         } else {
             g.rmf = (uint2 *)p;
-            g.rmb = (short2 *)(p + align256(sizeof(uint2) * (size_t)V.ox * V.oy));
+            g.rmb = (int2 *)(p + align256(sizeof(uint2) * (size_t)V.ox * V.oy));
             rm_ld = V.ox;
         }
         for (int a = 0; a < 2; ++a) {
@@ -1073,7 +1106,6 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         sa.prec = prec;
         sa.sc_g = scG;
         sa.sc_s = scS;
-        sa.energy = prec == NUFDS_FP16_STORE ? g.acc + kEnergyAcc : nullptr;
         hsoff[i] = tst;
         tst += stretch_tiles(sa.jn, V.npy);
         scSv[i] = scS;
@@ -1229,8 +1261,14 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         if (!rc && (where = "stretch"))
             rc = launch_stretch_batch((const StretchArgs *)(ddesc + o_sa),
                                       (const int *)(ddesc + o_soff), n, tst, prec, st);
-        for (int i = 0; i < n && !rc && prec == NUFDS_FP16_STORE; ++i)
-            rc = launch_scales_view(R[i].sc, R[i].acc, w[i].fpx->dmax, w[i].fpy->dmax, st);
+        for (int i = 0; i < n && !rc && prec == NUFDS_FP16_STORE; ++i) {
+            const BandWork &bw = bws[i];
+            rc = launch_energy((const char *)R[i].Bf + eb * (size_t)bw.bx0 * w[i].V.npy,
+                               (long)(bw.bx1 - bw.bx0) * w[i].V.npy, scSv[i],
+                               R[i].acc + kEnergyAcc, st);
+            if (!rc)
+                rc = launch_scales_view(R[i].sc, R[i].acc, w[i].fpx->dmax, w[i].fpy->dmax, st);
+        }
         auto rows_pass = [&](int pass) {
             int r = 0, item0 = pass == 0 ? 0 : (int)slots[0].size();
             for (int c = 0; c < kRowClasses && !r; ++c) {
@@ -1434,7 +1472,7 @@ int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream,
     P->pb_nkx = (int)(V.khi_x - V.klo_x + 1);
     P->pb_nky = (int)(V.khi_y - V.klo_y + 1);
     const size_t npb = (size_t)P->pb_nkx * P->pb_nky, npix = (size_t)P->nx * P->ny;
-    P->fixed_bytes = npb * 12 + npix * 12 + npix * 4 * prec_bytes(P->prec) + 64;
+    P->fixed_bytes = npb * 12 + npix * 16 + npix * 4 * prec_bytes(P->prec) + 64;
     if (P->budget && P->fixed_bytes > P->budget) {
         free_plan(P);
         return NUFDS_ENOMEM;
@@ -1778,7 +1816,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     float2 *G = c.take<float2>(4 * npix);
     short2 *pbb = c.take<short2>((size_t)pb_nkx * pb_nky);
     float2 *pbf = c.take<float2>((size_t)pb_nkx * pb_nky);
-    short2 *rmb = c.take<short2>(npix);
+    int2 *rmb = c.take<int2>(npix);
     uint2 *rmf = c.take<uint2>(npix);
     float2 *A = c.take<float2>(4 * (np2 > npix ? np2 : npix));
     float2 *Bf = c.take<float2>(2 * (np2 > npix ? np2 : npix));
@@ -1799,14 +1837,14 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
         Ey = c.take<OutChirp>(nby);
         if (!Ex || !Ey) return NUFDS_EUNSUPPORTED;
     }
-    short2 *vrb = rmb;
+    int2 *vrb = rmb;
     uint2 *vrf = rmf;
     long rm_ld = nx, rm_i0 = 0, rm_j0 = 0;
     if (V.lattice) {
         rm_i0 = V.i0;
         rm_j0 = V.j0;
     } else {
-        vrb = c.take<short2>((size_t)V.ox * V.oy);
+        vrb = c.take<int2>((size_t)V.ox * V.oy);
         vrf = c.take<uint2>((size_t)V.ox * V.oy);
         rm_ld = V.ox;
     }
@@ -1864,7 +1902,6 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     sa.prec = PREC_F32;
     sa.sc_g = nullptr;
     sa.sc_s = nullptr;
-    sa.energy = nullptr;
     sa.plain = 0;
     if ((rc = launch_stretch(sa, st)) ||
         (rc = launch_rows_view(fpy, Bf, V.npy, chy, A, 2 * V.npy, V.npx, scr, grid_y, PREC_F32,

@@ -669,6 +669,93 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
     }
 }
 
+// Padded forward pass of a split row (the hologram's passes when N > kMaxRowL):
+// CTA c transforms the samples 2m + c (times the deapodisation and, for the
+// odd half, the modulation), then the halves combine as in split_combine.
+template <int R, class TI>
+__device__ __forceinline__ void pad_first_split_r(const PassArgs &P, const TI *__restrict__ irow,
+                                                  float inv, float2 *sm, int a, int c) {
+    const int nb = P.L / R;
+    for (int n = threadIdx.x; n < nb; n += blockDim.x) {
+        float2 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int m = 2 * (n + i * nb) + c;
+            float2 v = cscale(ld_cs(irow, m, inv), __ldg(P.pad_pre + m));
+            x[i] = a ? cmul(v, __ldg(P.mod1 + m)) : v;
+        }
+        Dft<R, false>::run(x);
+        uint32_t q = n;
+        int base = 0;
+        for (int j = 0; j < P.npass - 1; ++j) {
+            uint32_t q2 = udiv(q, P.mag_radix[j]);
+            base += (int)(q - q2 * P.radix[j]) * P.stride[j];
+            q = q2;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) sm[phys(base + k)] = x[k];
+    }
+}
+
+// outputs k = c L/2 + k' of half a of a split padded row, (-1)^k (Z_0[k'] +
+// W_L^k Z_1[k']), in the layout P.natural_out selects (2: the even half waits
+// in pscr, this CTA's L/2 entries, and each fine pair is stored together)
+template <class TO>
+__device__ __forceinline__ void split_combine_pad(const PassArgs &P, const float2 *sm,
+                                                  const float2 *peer, const float2 *twl, int c,
+                                                  TO *__restrict__ orow, float sc, int a,
+                                                  float2 *__restrict__ pscr) {
+    const int Lh = P.L;
+    for (int k = threadIdx.x; k < Lh; k += blockDim.x) {
+        const float2 zo = sm[phys(k)], zp = peer[phys(k)];
+        const float2 z0 = c ? zp : zo, z1 = c ? zo : zp;
+        float2 t = cmul(z1, twl_at(twl, k));
+        if (c) t = make_float2(-t.x, -t.y);
+        float2 v = cadd(z0, t);
+        const long f = (long)c * Lh + k;
+        if (f & 1) v = make_float2(-v.x, -v.y);
+        if (P.natural_out == 2) {
+            if (a == 0) pscr[k] = v;
+            else st_pair(orow, f, pscr[k], v, sc);
+        } else {
+            st_cs(orow, P.natural_out ? 2 * f + a : a * P.Lfull + f, v, sc);
+        }
+    }
+}
+
+template <class TI, class TO>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512)
+    k_rows_pad2_split(PassArgs P, const TI *__restrict__ in, long in_ld, TO *__restrict__ out,
+                      long out_ld, int rows, const float *sc_in, const float *sc_out,
+                      float2 *pair_scr) {
+    extern __shared__ float2 sm[];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)cl.block_rank();
+    const float2 *peer = cl.map_shared_rank(sm, c ^ 1);
+    const float2 *tws = load_tw(P, sm);
+    float2 *twl = sm + phys(P.L) + 1 + 64 + P.ncoarse;
+    for (int i = threadIdx.x; i < 64 + (P.L + 63) / 64; i += blockDim.x) twl[i] = P.twL[i];
+    __syncthreads();
+    const float inv = sc_in ? 1.0f / *sc_in : 1.0f, sc = sc_out ? *sc_out : 1.0f;
+    const int RL = P.radix[P.npass - 1];
+    float2 *pscr = pair_scr ? pair_scr + (long)blockIdx.x * P.L : nullptr;
+    for (int r = blockIdx.x >> 1; r < rows; r += gridDim.x >> 1) {
+        const TI *irow = in + (long)r * in_ld;
+        TO *orow = out + (long)r * out_ld;
+        for (int a = 0; a < 2; ++a) {
+#define C_(R) pad_first_split_r<R, TI>(P, irow, inv, sm, a, c)
+            NUFDS_RADIX_SWITCH(RL, C_)
+#undef C_
+            __syncthreads();
+            forward_tail_smem(P, sm, tws);
+            cl.sync();
+            split_combine_pad<TO>(P, sm, peer, twl, c, orow, sc, a, pscr);
+            cl.sync();
+        }
+    }
+}
+
 // ------------------------------------------------------------------------
 // host side: plans and tables
 // ------------------------------------------------------------------------
@@ -1121,6 +1208,11 @@ static void set_smem_attrs(size_t bytes) {
         cudaFuncSetAttribute(k_rows_view_batch<__half2>, a, m);
         cudaFuncSetAttribute(k_rows_view_batch<__nv_bfloat162>, a, m);
         cudaFuncSetAttribute(k_rows_view_split<float2>, a, m);
+        cudaFuncSetAttribute(k_rows_pad2_split<float2, float2>, a, m);
+        cudaFuncSetAttribute(k_rows_pad2_split<float2, __half2>, a, m);
+        cudaFuncSetAttribute(k_rows_pad2_split<float2, __nv_bfloat162>, a, m);
+        cudaFuncSetAttribute(k_rows_pad2_split<__half2, __half2>, a, m);
+        cudaFuncSetAttribute(k_rows_pad2_split<__nv_bfloat162, __nv_bfloat162>, a, m);
         cudaFuncSetAttribute(k_rows_view_split<__half2>, a, m);
         cudaFuncSetAttribute(k_rows_view_split<__nv_bfloat162>, a, m);
     }
@@ -1154,15 +1246,39 @@ int launch_rows_pad2(const FftPlan &p, const void *in, int in_prec, long in_ld, 
                      cudaStream_t st, int natural_out, const float *pre, float2 *pair_scr,
                      size_t pair_cap) {
     if (rows <= 0) return 0;
-    if (p.split != 1) return -3;  // hologram rows are at most kMaxRowL long
     FftPlan q = p;
     q.threads = p.pad_threads;
-    const int grid = grid_for((const void *)k_rows_pad2<float2, float2>, q, rows);
+    int grid;
+    if (p.split == 2) {  // two CTAs per row: an even grid of at most the resident CTAs
+        int dev, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, (const void *)k_rows_pad2_split<float2, float2>, q.threads, p.smem_bytes);
+        long g = std::min((long)sms * (per < 1 ? 1 : per), 2L * rows);
+        grid = (int)std::max(2L, g & ~1L);
+    } else {
+        grid = grid_for((const void *)k_rows_pad2<float2, float2>, q, rows);
+    }
     PassArgs a = fft_pass_args(p);
     a.natural_out = natural_out;
     if (pre) a.pad_pre = pre;
     if (!natural_out || (size_t)grid * p.L > pair_cap) pair_scr = nullptr;
     if (pair_scr) a.natural_out = 2;
+    if (p.split == 2) {
+#define L_(TI, TO)                                                                         \
+    k_rows_pad2_split<TI, TO><<<grid, q.threads, p.smem_bytes, st>>>(                      \
+        a, (const TI *)in, in_ld, (TO *)out, out_ld, rows, sc_in, sc_out, pair_scr)
+        if (in_prec == PREC_F32 && prec == PREC_F32) L_(float2, float2);
+        else if (in_prec == PREC_F32 && prec == PREC_F16) L_(float2, __half2);
+        else if (in_prec == PREC_F32 && prec == PREC_BF16) L_(float2, __nv_bfloat162);
+        else if (in_prec == PREC_F16 && prec == PREC_F16) L_(__half2, __half2);
+        else if (in_prec == PREC_BF16 && prec == PREC_BF16) L_(__nv_bfloat162, __nv_bfloat162);
+        else return -3;
+#undef L_
+        count_launch();
+        return check_launch();
+    }
 #define L_(TI, TO)                                                                        \
     k_rows_pad2<TI, TO><<<grid, q.threads, p.smem_bytes, st>>>(a, (const TI *)in, in_ld,  \
                                                               (TO *)out, out_ld, rows,    \
@@ -1317,19 +1433,35 @@ int launch_transpose_batch(const TrItem *d_items, const int *d_tile_off, int nit
 }
 
 // Weighted energies of the hologram for the FP16 scales of the padded passes:
-// acc[0] += sum |h|^2 dx[ix]^2, acc[1] += sum |h|^2 dx[ix]^2 dy[iy]^2.
+// acc[0] += sum |h|^2 dx[ix]^2, acc[1] += sum |h|^2 dx[ix]^2 dy[iy]^2.  Terms in
+// FP32, summed in FP32 over runs of kNormRun elements and in FP64 across runs
+// (the scales need a bound, not an exact sum: k_scales_load widens it).
+constexpr int kNormRun = 64;
 __global__ void k_norms(const float2 *__restrict__ H, int nx, int ny, const double *__restrict__ dx,
                         const double *__restrict__ dy, double *acc) {
     double s0 = 0, s1 = 0;
-    const long n = (long)nx * ny;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long)gridDim.x * blockDim.x) {
-        const int iy = (int)(i / nx), ix = (int)(i - (long)iy * nx);
-        const float2 v = H[i];
-        const double e = (double)v.x * v.x + (double)v.y * v.y, wx = dx[ix] * dx[ix];
-        s0 += e * wx;
-        s1 += e * wx * dy[iy] * dy[iy];
+    float r0 = 0.f, r1 = 0.f;
+    int k = 0;
+    // rows by blocks, columns by threads (no index division per sample)
+    for (int iy = blockIdx.x; iy < ny; iy += gridDim.x) {
+        const float wy = (float)dy[iy], wy2 = wy * wy;
+        const float2 *row = H + (long)iy * nx;
+        for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+            const float2 v = __ldcs(row + ix);
+            const float wx = (float)dx[ix];
+            const float e = fmaf(v.x, v.x, v.y * v.y) * wx * wx;
+            r0 += e;
+            r1 = fmaf(e, wy2, r1);
+            if (++k == kNormRun) {
+                s0 += r0;
+                s1 += r1;
+                r0 = r1 = 0.f;
+                k = 0;
+            }
+        }
     }
+    s0 += r0;
+    s1 += r1;
     for (int o = 16; o; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -1338,6 +1470,44 @@ __global__ void k_norms(const float2 *__restrict__ H, int nx, int ny, const doub
         atomicAdd(acc, s0);
         atomicAdd(acc + 1, s1);
     }
+}
+
+// ||S||^2 of the stretched band for the FP16 scales of the view passes, from
+// the stored S (count elements held as S sc; FP32 terms and runs, FP64 across
+// runs, one atomic per warp spread over kEnergySlots slots).
+__global__ void k_energy(const __half2 *__restrict__ S, long count, const float *sc_s,
+                         double *slots) {
+    const float inv = 1.0f / *sc_s;
+    double s = 0;
+    float r = 0.f;
+    int k = 0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long)gridDim.x * blockDim.x) {
+        const float2 v = __half22float2(__ldg(S + i));
+        r = fmaf(v.x, v.x, fmaf(v.y, v.y, r));
+        if (++k == kNormRun) {
+            s += r;
+            r = 0.f;
+            k = 0;
+        }
+    }
+    s += r;
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0)
+        atomicAdd(slots + ((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (kEnergySlots - 1)),
+                  s * (double)inv * (double)inv);
+}
+
+int launch_energy(const void *S, long count, const float *sc_s, double *slots, cudaStream_t st) {
+    if (cudaMemsetAsync(slots, 0, kEnergySlots * sizeof(double), st) != cudaSuccess) return -4;
+    if (count <= 0) return 0;
+    int dev, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long blocks = std::min((long)sms * 4, (count + 255) / 256);
+    k_energy<<<(int)blocks, 256, 0, st>>>((const __half2 *)S, count, sc_s, slots);
+    count_launch();
+    return check_launch();
 }
 
 int launch_norms(const float2 *H, int nx, int ny, const double *dx, const double *dy, double *acc,
@@ -1362,8 +1532,9 @@ __device__ __forceinline__ float pow2_scale(double bound) {
 // Parseval bounds (max |.| <= Frobenius norm):
 //   |T1| <= sqrt(2 Nx) ||h dx||,  |G| <= 2 sqrt(Nx Ny) ||h dx dy||,  |S| <= K2 |G|
 __global__ void k_scales_load(float *sc, const double *acc, int nx, int ny, double k2) {
-    const double bT1 = sqrt(2.0 * nx * acc[0]);
-    const double bG = 2.0 * sqrt((double)nx * ny * acc[1]);
+    // the energies are sums of FP32 terms: widen by 1e-3 to keep the bounds
+    const double bT1 = sqrt(2.0 * nx * acc[0] * 1.001);
+    const double bG = 2.0 * sqrt((double)nx * ny * acc[1] * 1.001);
     sc[0] = pow2_scale(bT1);
     sc[1] = pow2_scale(bG);
     sc[2] = pow2_scale(k2 * bG);
@@ -1373,7 +1544,7 @@ __global__ void k_scales_load(float *sc, const double *acc, int nx, int ny, doub
 __global__ void k_scales_view(float *sc, const double *acc, double dxp, double dyp) {
     double e = 0;
     for (int k = 0; k < kEnergySlots; ++k) e += acc[kEnergyAcc + k];
-    const double nS = sqrt(e);
+    const double nS = sqrt(e * 1.01);  // from FP16-rounded S, summed in FP32 runs: widened
     sc[3] = pow2_scale(sqrt(2.0) * dyp * nS);
     sc[4] = sc[3];
     sc[5] = pow2_scale(2.0 * dxp * dyp * nS);

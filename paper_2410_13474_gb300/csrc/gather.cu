@@ -118,6 +118,7 @@ __device__ __forceinline__ int wrap(int m, int M) {
     return m < 0 ? m + M : (m >= M ? m - M : m);
 }
 
+
 // sum_{i,j} wr[i] wc[j] A[row r0 + i][column c0 + j] for a window inside a
 // grid stored plane-wise on both axes (fine row m at row (m & 1) Lr + (m >> 1),
 // pitch ld; fine column m at (m & 1) Lc + (m >> 1)): 0 <= r0, r0 + kW <= 2 Lr,
@@ -289,18 +290,19 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
     const bool inside = jx - a.jx0 < (a.jn ? a.jn : a.npx) && jx < a.npx && jy < a.npy;
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
     bool valid = false;
-    short2 b = make_short2(0, 0);
+    int2 b = make_int2(0, 0);
     float2 f = make_float2(0.f, 0.f);
     if (inside && kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
         if (a.plain) {  // f = f'_k: fine position 2k, zero outside |f| <= 1/(2 pitch)
             if (2 * labs(kx) <= a.Nx && 2 * labs(ky) <= a.Ny) {
-                b = make_short2((short)(2 * kx), (short)(2 * ky));
+                b = make_int2((int)(2 * kx), (int)(2 * ky));
                 valid = true;
             }
         } else {
             const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
-            b = a.pb_base[t];
-            if (b.x != kMasked) {
+            const short2 e = a.pb_base[t];
+            if (e.x != kMasked) {
+                b = make_int2(e.x + (int)(2 * kx), e.y + (int)(2 * ky));
                 f = a.pb_frac[t];
                 valid = true;
             }
@@ -339,21 +341,6 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
         acc = make_float2(acc.x * ginv, acc.y * ginv);
     }
     if (inside) st_c((T *)a.S, (long)jx * a.npy + jy, acc, ssc);
-    if (a.energy) {  // uniform over the launch; every thread reaches the barrier
-        // one atomic per CTA, spread over kEnergySlots addresses (a single
-        // address serialises the atomics of every warp of the launch)
-        __shared__ double red[8];
-        double e = (double)acc.x * acc.x + (double)acc.y * acc.y;
-        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        const int wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-        if ((threadIdx.x & 31) == 0) red[wid] = e;
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            double t = 0;
-            for (int k = 0; k < (int)(blockDim.x * blockDim.y) >> 5; ++k) t += red[k];
-            atomicAdd(a.energy + ((bx + by) & (kEnergySlots - 1)), t);
-        }
-    }
 }
 
 template <class T>
@@ -380,7 +367,7 @@ __global__ void __launch_bounds__(256, 4) k_stretch_batch(const StretchArgs *__r
     stretch_body<T>(a, t % tx, t / tx);
 }
 
-__device__ __forceinline__ void remap_store(const RemapArgs &a, long o, float2 acc, short2 b,
+__device__ __forceinline__ void remap_store(const RemapArgs &a, long o, float2 acc, int2 b,
                                             uint2 F);
 
 template <class T>
@@ -390,7 +377,7 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const int i = bx * 32 + threadIdx.x;
     const int j = by * 8 + threadIdx.y;
     const bool valid = i < a.ox && j < a.oy;
-    short2 b = make_short2(0, 0);
+    int2 b = make_int2(0, 0);
     uint2 F = make_uint2(0u, 0u);
     if (valid) {
         const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
@@ -434,7 +421,7 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
 
 // O = P at the output pixel o: |O|^2, added |O|^2, or O times the output chirp
 // of the fine position b + F 2^-32
-__device__ __forceinline__ void remap_store(const RemapArgs &a, long o, float2 acc, short2 b,
+__device__ __forceinline__ void remap_store(const RemapArgs &a, long o, float2 acc, int2 b,
                                             uint2 F) {
     if (a.kind == 0) {
         ((float *)a.out)[o] = fmaf(acc.x, acc.x, acc.y * acc.y);
@@ -494,18 +481,19 @@ __global__ void __launch_bounds__(256) k_stretch_linear(StretchArgs a) {
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
     float2 acc = make_float2(0.f, 0.f);
     bool valid = false;
-    short2 b = make_short2(0, 0);
+    int2 b = make_int2(0, 0);
     float2 f = make_float2(0.f, 0.f);
     if (kx >= a.klo_x && kx <= a.khi_x && ky >= a.klo_y && ky <= a.khi_y) {
         if (a.plain) {
             if (2 * labs(kx) <= a.Nx && 2 * labs(ky) <= a.Ny) {
-                b = make_short2((short)(2 * kx), (short)(2 * ky));
+                b = make_int2((int)(2 * kx), (int)(2 * ky));
                 valid = true;
             }
         } else {
             const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
-            b = a.pb_base[t];
-            if (b.x != kMasked) {
+            const short2 e = a.pb_base[t];
+            if (e.x != kMasked) {
+                b = make_int2(e.x + (int)(2 * kx), e.y + (int)(2 * ky));
                 f = a.pb_frac[t];
                 valid = true;
             }
@@ -526,7 +514,7 @@ __global__ void __launch_bounds__(256) k_remap_linear(RemapArgs a) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     if (i >= a.ox || j >= a.oy) return;
     const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
-    const short2 b = a.rm_base[t];
+    const int2 b = a.rm_base[t];
     const uint2 F = a.rm_frac[t];
     const int px = (int)(b.x - 2 * a.kc_x), py = (int)(b.y - 2 * a.kc_y);
     const float fx = __uint2float_rz(F.x) * 0x1p-32f, fy = __uint2float_rz(F.y) * 0x1p-32f;

@@ -62,8 +62,9 @@ __device__ __forceinline__ void st_c(__nv_bfloat162 *p, long i, float2 v, float)
 }
 
 // Entry of a coordinate table: a point on a fine (2x oversampled) grid as
-// centred integer base (floor of 2t) and fraction in [0, 1).
-// base.x == kMasked marks a point that is zeroed.
+// centred integer base (floor of 2t, in the pull-back table as its offset
+// from 2k) and fraction in [0, 1).  base.x == kMasked marks a point that is
+// zeroed.
 constexpr int16_t kMasked = -32768;
 
 // ---------------------------------------------------------------------------
@@ -218,9 +219,14 @@ void host_phi(double u, double v, double *up, double *vp,
 double g_at_one();
 
 // Pull-back table over lattice [kx0, kx0+nkx) x [ky0, ky0+nky), layout [kx][ky].
+// With coarse (device memory of pullback_coarse_count(nkx, nky) double2),
+// the pre-images of every kPullbackStep-th point are solved first and seed
+// the others' Newton iterations.
+constexpr int kPullbackStep = 16;
+int pullback_coarse_count(int nkx, int nky);
 int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
                           int nky, short2 *base, float2 *frac, cudaStream_t st,
-                          const MapFn &m = MapFn());
+                          const MapFn &m = MapFn(), double2 *coarse = nullptr);
 // Output-map table for pixels x_o = cx + (i - ox/2) px etc. at distance z,
 // layout [j][i]; t' in stretched-lattice units, stored as b = floor(2t') and
 // the fraction 2t' - b in 0.32 fixed point (exact to 2^-32 of a fine cell:
@@ -228,7 +234,7 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
 // the paper's depths, so an FP32 fraction would cost 1e-4 rad).
 // plain = 1: the identity map x' = x_o of the plain Fresnel transform instead.
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
-                       double px, double py, int ox, int oy, short2 *base, uint2 *frac,
+                       double px, double py, int ox, int oy, int2 *base, uint2 *frac,
                        cudaStream_t st, int plain = 0, const MapFn &m = MapFn());
 // chirp[slot] = e^{i pi x_n^2/(lambda z)} deapod[n] / L (linear: 1 / L) at n = natural index of the
 // slot (digit-reversed order of plan fp), x_n = (n - L/2) window / L
@@ -271,7 +277,7 @@ inline uint2 turns_fx32(double turns) {
 struct StretchArgs {
     const void *G;          // oversampled spectrum, layout [mx][my], 2Nx x 2Ny
     int Nx, Ny;
-    const short2 *pb_base;  // pull-back table, layout [kx][ky]
+    const short2 *pb_base;  // pull-back table, layout [kx][ky]: fine base - 2 k (kMasked: zero)
     const float2 *pb_frac;
     long pb_kx0, pb_ky0;
     int pb_nkx, pb_nky;
@@ -282,8 +288,6 @@ struct StretchArgs {
     void *S;                // output, layout [jx][jy], npx x npy
     int prec;               // storage of G and S
     const float *sc_g, *sc_s;
-    double *energy;         // if not null: sum |S|^2 (before storage rounding) added over
-                            // energy[0 .. kEnergySlots), zeroed by the caller
     int plain;              // 1: no stretch, S(f'_k) = DTFT at f = f'_k (plain FrT)
     int linear;             // 1: bilinear on the unpadded DFT grid (G's even samples of
                             //    the hologram loaded without deapodisation)
@@ -298,7 +302,7 @@ struct RemapArgs {
     const void *Q;          // oversampled FrT output, layout [my][mx], 2npy x 2npx
     int npx, npy;
     long kc_x, kc_y;
-    const short2 *rm_base;  // output-map table, layout [j][i], row length rm_ld
+    const int2 *rm_base;    // output-map table, layout [j][i], row length rm_ld
     const uint2 *rm_frac;   // its fractions, 0.32 fixed point
     long rm_ld, rm_i0, rm_j0;
     int ox, oy;
@@ -322,11 +326,14 @@ inline int remap_tiles(int ox, int oy) { return ((ox + 31) / 32) * ((oy + 7) / 8
 //   sc[0] T1, sc[1] G, sc[2] S, sc[3] T_T, sc[4] T, sc[5] Q; each the largest
 //   power of two with scale * bound <= 2^15.  acc[] (device doubles): [0], [1]
 //   weighted hologram energies (launch_norms), [kEnergyAcc, kEnergyAcc +
-//   kEnergySlots) partial sums of ||S||^2 (the stretch).
+//   kEnergySlots) partial sums of ||S||^2 (launch_energy).
 constexpr int kEnergySlots = 16;
 constexpr int kEnergyAcc = 8;
 int launch_norms(const float2 *H, int nx, int ny, const double *dx, const double *dy, double *acc,
                  cudaStream_t st);
+// ||S||^2 of count FP16 elements stored as S sc_s, into slots[0 .. kEnergySlots)
+// (zeroed first)
+int launch_energy(const void *S, long count, const float *sc_s, double *slots, cudaStream_t st);
 int launch_scales_load(float *sc, const double *acc, int nx, int ny, double k2, cudaStream_t st);
 int launch_scales_view(float *sc, const double *acc, double dxp, double dyp, cudaStream_t st);
 

@@ -157,12 +157,18 @@ __device__ inline void jac_uv(double u, double v, double g1, const MapFn &m, dou
 }
 
 // Inverse of the stretch: solve phi(u, v) = (up, vp) inside the unit disc by
-// damped Newton.  Returns false when (up, vp) has no pre-image.
+// damped Newton, from (u0, v0) when given inside the disc (an interpolated
+// neighbouring solution), else from (up, vp) pulled inside radius 0.9.
+// Returns false when (up, vp) has no pre-image.
 __device__ bool pullback_uv(double up, double vp, double g1, const MapFn &m, double tol, double *uo,
-                            double *vo) {
+                            double *vo, double u0 = 2.0, double v0 = 0.0) {
     double u = up, v = vp;
+    if (u0 * u0 + v0 * v0 < 0.99) {
+        u = u0;
+        v = v0;
+    }
     double rr = u * u + v * v;
-    if (rr > 0.81) {
+    if (rr > 0.81 && !(u0 * u0 + v0 * v0 < 0.99)) {
         double sc = 0.9 * rsqrt(rr);
         u *= sc;
         v *= sc;
@@ -207,31 +213,70 @@ __device__ bool pullback_uv(double up, double vp, double g1, const MapFn &m, dou
     return false;
 }
 
-__device__ inline void split_fine(double t2, short *base, float *frac) {
+// the fine base as an offset from 2k (the identity map) and the FP32 fraction
+__device__ inline void split_fine(double t2, long k2, short *base, float *frac) {
     double b = floor(t2);
-    *base = (short)b;
+    *base = (short)((long)b - k2);
     *frac = (float)(t2 - b);
 }
 
+// Coarse solutions for the pull-back table: the pre-image (u, v) of every
+// step-th lattice point of the band (and of its last row and column), NaN
+// where there is none.  Node c of an axis sits at min(c step, n - 1).
+__global__ void k_pullback_coarse(double lam, double pitch, int nx, int ny, long kx0, int nkx,
+                                  long ky0, int nky, int step, int ncx, int ncy, double g1,
+                                  MapFn m, double2 *cuv) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)ncx * ncy) return;
+    const int cx = (int)(idx / ncy), cy = (int)(idx - (long)cx * ncy);
+    const int ix = min(cx * step, nkx - 1), iy = min(cy * step, nky - 1);
+    const double up = lam * (double)(kx0 + ix) / (nx * pitch);
+    const double vp = lam * (double)(ky0 + iy) / (ny * pitch);
+    double u, v;
+    if (pullback_uv(up, vp, g1, m, 1e-13 * lam / pitch, &u, &v)) cuv[idx] = make_double2(u, v);
+    else cuv[idx] = make_double2(NAN, NAN);
+}
+
 // Table of f(f'_k) for lattice points k of the stretched band, layout [kx][ky]:
-// fine coordinates 2 t with t = N pitch f (centred grid units).  Masked where
-// there is no pre-image or |t_x| > N_x/2 or |t_y| > N_y/2.
+// fine coordinates 2 t with t = N pitch f (centred grid units), the integer
+// base stored as its offset from 2 k (|2 t - 2 k| stays far below 2^15 while
+// 2 t itself reaches +-N), the fraction in FP32.  Masked (base.x = kMasked)
+// where there is no pre-image or |t_x| > N_x/2 or |t_y| > N_y/2.  With coarse
+// solutions (cuv), Newton starts from their bilinear interpolation when the
+// four surrounding ones exist (one or two steps instead of several from the
+// identity; the same root and the same stopping rule).
 __global__ void k_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx,
                                  long ky0, int nky, double g1, MapFn m, short2 *base,
-                                 float2 *frac) {
+                                 float2 *frac, const double2 *cuv, int step, int ncx, int ncy) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)nkx * nky) return;
     int ix = (int)(idx / nky), iy = (int)(idx - (long)ix * nky);
     double up = lam * (double)(kx0 + ix) / (nx * pitch);
     double vp = lam * (double)(ky0 + iy) / (ny * pitch);
+    double u0 = 2.0, v0 = 0.0;  // no start given
+    if (cuv) {
+        const int cx = min(ix / step, ncx - 2), cy = min(iy / step, ncy - 2);
+        const int x0 = cx * step, x1 = min((cx + 1) * step, nkx - 1);
+        const int y0 = cy * step, y1 = min((cy + 1) * step, nky - 1);
+        const double ax = x1 > x0 ? (double)(ix - x0) / (x1 - x0) : 0.0;
+        const double ay = y1 > y0 ? (double)(iy - y0) / (y1 - y0) : 0.0;
+        const double2 c00 = cuv[(long)cx * ncy + cy], c01 = cuv[(long)cx * ncy + cy + 1];
+        const double2 c10 = cuv[(long)(cx + 1) * ncy + cy], c11 = cuv[(long)(cx + 1) * ncy + cy + 1];
+        const double su = (1 - ax) * ((1 - ay) * c00.x + ay * c01.x) + ax * ((1 - ay) * c10.x + ay * c11.x);
+        const double sv = (1 - ax) * ((1 - ay) * c00.y + ay * c01.y) + ax * ((1 - ay) * c10.y + ay * c11.y);
+        if (su == su && sv == sv) {  // all four corners solved (NaN propagates)
+            u0 = su;
+            v0 = sv;
+        }
+    }
     double u, v;
     short2 b = make_short2(kMasked, kMasked);
     float2 f = make_float2(0.f, 0.f);
-    if (pullback_uv(up, vp, g1, m, 1e-13 * lam / pitch, &u, &v)) {
+    if (pullback_uv(up, vp, g1, m, 1e-13 * lam / pitch, &u, &v, u0, v0)) {
         double tx = nx * pitch * u / lam, ty = ny * pitch * v / lam;
         if (fabs(tx) <= 0.5 * nx && fabs(ty) <= 0.5 * ny) {
-            split_fine(2.0 * tx, &b.x, &f.x);
-            split_fine(2.0 * ty, &b.y, &f.y);
+            split_fine(2.0 * tx, 2 * (kx0 + ix), &b.x, &f.x);
+            split_fine(2.0 * ty, 2 * (ky0 + iy), &b.y, &f.y);
         }
     }
     base[idx] = b;
@@ -239,9 +284,9 @@ __global__ void k_pullback_table(double lam, double pitch, int nx, int ny, long 
 }
 
 // floor and 0.32 fixed-point fraction (truncated, so the fraction is < 1)
-__device__ inline void split_fine_fx(double t2, short *base, unsigned int *frac) {
+__device__ inline void split_fine_fx(double t2, int *base, unsigned int *frac) {
     double b = floor(t2);
-    *base = (short)b;
+    *base = (int)b;
     double q = floor((t2 - b) * 4294967296.0);
     *frac = q >= 4294967295.0 ? 0xffffffffu : (unsigned int)q;
 }
@@ -250,7 +295,7 @@ __device__ inline void split_fine_fx(double t2, short *base, unsigned int *frac)
 // f_0 = (x_o, y_o) / (lambda R_0), for view pixels; layout [j][i].
 __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z, double cx,
                               double cy, double px, double py, int ox, int oy, double g1,
-                              MapFn m, short2 *base, uint2 *frac, int plain) {
+                              MapFn m, int2 *base, uint2 *frac, int plain) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)ox * oy) return;
     int j = (int)(idx / ox), i = (int)(idx - (long)j * ox);
@@ -264,7 +309,7 @@ __global__ void k_remap_table(double lam, double pitch, int nx, int ny, double z
         phi_uv(xo / R0, yo / R0, g1, m, &up, &vp);
     }
     double tx = nx * pitch * up / lam, ty = ny * pitch * vp / lam;
-    short2 b;
+    int2 b;
     uint2 f;
     split_fine_fx(2.0 * tx, &b.x, &f.x);
     split_fine_fx(2.0 * ty, &b.y, &f.y);
@@ -332,18 +377,35 @@ __global__ void k_outchirp_table(double kappa, long b0, int nb, OutChirp *E) {
     E[i] = o;
 }
 
+int pullback_coarse_count(int nkx, int nky) {
+    const int ncx = (nkx - 1 + kPullbackStep - 1) / kPullbackStep + 1;
+    const int ncy = (nky - 1 + kPullbackStep - 1) / kPullbackStep + 1;
+    return ncx * ncy;
+}
+
 int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, int nkx, long ky0,
-                          int nky, short2 *base, float2 *frac, cudaStream_t st, const MapFn &m) {
+                          int nky, short2 *base, float2 *frac, cudaStream_t st, const MapFn &m,
+                          double2 *coarse) {
     long n = (long)nkx * nky;
     if (n <= 0) return 0;
-    k_pullback_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lam, pitch, nx, ny, kx0, nkx,
-                                                                 ky0, nky, g_at_one(), m, base, frac);
+    const int step = kPullbackStep;
+    const int ncx = (nkx - 1 + step - 1) / step + 1, ncy = (nky - 1 + step - 1) / step + 1;
+    if (coarse && (ncx < 2 || ncy < 2)) coarse = nullptr;
+    if (coarse) {
+        const long nc = (long)ncx * ncy;
+        k_pullback_coarse<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(
+            lam, pitch, nx, ny, kx0, nkx, ky0, nky, step, ncx, ncy, g_at_one(), m, coarse);
+        count_launch();
+        if (check_launch()) return -4;
+    }
+    k_pullback_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+        lam, pitch, nx, ny, kx0, nkx, ky0, nky, g_at_one(), m, base, frac, coarse, step, ncx, ncy);
     count_launch();
     return check_launch();
 }
 
 int launch_remap_table(double lam, double pitch, int nx, int ny, double z, double cx, double cy,
-                       double px, double py, int ox, int oy, short2 *base, uint2 *frac,
+                       double px, double py, int ox, int oy, int2 *base, uint2 *frac,
                        cudaStream_t st, int plain, const MapFn &m) {
     long n = (long)ox * oy;
     if (n <= 0) return 0;
