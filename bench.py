@@ -20,8 +20,10 @@ over the dominant kernel's time, with the design's own bytes beside them),
 p50/p99 of the step and of a view on the loaded hologram, per-stage times,
 the clocks seen, the 16 partial views, the storage-precision and
 paper-literal variants, cuFFT (torch.fft) timed on the same transform sizes
-as a comparison, and the FP64 oracle timed on the host cores on a bounded
-sample (cpu_baseline).  Other workloads: --workload wa4096 | small512 (the
+as a comparison, the FP64 oracle timed on the host cores on a bounded
+sample (cpu_baseline), and a serving block (2000 Poisson requests at
+200/s over 12 resident holograms, continuous batching against one request
+at a time, p50/p99).  Other workloads: --workload wa4096 | small512 (the
 stated 4096^2 at 3 mm and 512^2 at 1 mm), uwa16k-paper-depths |
 wa4096-paper-depths | small512-paper-depths (the paper's metre depths),
 strip16k | batch64 | serve | sweep16k.
@@ -693,6 +695,16 @@ def run_ours(args, w):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     plan.close()
+    del out, ref_out, d_holo
+    torch.cuda.empty_cache()
+    if world == 1 and args.serve_requests > 0:
+        # serving: resident holograms, a Poisson stream of view requests,
+        # continuous batching against one request at a time (p50/p99 latency)
+        try:
+            line["serve"] = serve_block(args.serve_requests, args.rate)
+        except RuntimeError as e:
+            torch.cuda.empty_cache()
+            line["serve"] = {"error": str(e).splitlines()[0][:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -775,7 +787,10 @@ def run_batch(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     from paper_2410_13474_gb300 import build as b
     b.build()
-    holos, reqs = batch_workload()
+    from synth import configs
+    stated = args.workload == "batch64"
+    holos, reqs = (batch_workload(z_range=configs.BATCH_Z_MM, max_fft=configs.MAX_FFT) if stated
+                   else batch_workload())
     t0 = time.time()
     plans = []
     for w in holos:
@@ -826,7 +841,10 @@ def run_batch(args):
     line = {"metric": "batched partial views/s (64 views, 8 holograms)",
             "value": res["batched"]["views_per_s"], "unit": "views/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch-64-views-8-holograms",
+            "config": {"workload": "batch-64-views-8-holograms" + ("" if stated else "-paper-depths"),
+                       "view_z_m": [min(r.z for r in reqs), max(r.z for r in reqs)],
+                       "np_max": max(max(pl.view_plan(v)["np_x"], pl.view_plan(v)["np_y"])
+                                     for pl, v in zip(vplans, views)),
                        "holograms": [[w.n, round(w.pitch * 1e6, 4), w.n_points] for w in holos],
                        "view_sizes": sorted({r.size for r in reqs}), "views": len(reqs),
                        "output_Mpix_per_batch": round(pix / 1e6, 2)},
@@ -838,6 +856,92 @@ def run_batch(args):
         pl.close()
 
 
+class ServePool:
+    """The serving workload's resident holograms (plans) and a seeded Poisson
+    stream of view requests over them; serve() runs a stream continuously
+    batched on two streams under an HBM budget, or one request at a time with
+    the plain single-view call.  stated: the millimetre depths given for the
+    benchmark (else the paper's metre depths)."""
+
+    def __init__(self, nreq, rate, stated=True):
+        import torch
+
+        import paper_2410_13474_gb300 as nf
+        import synth
+        from synth import configs
+        kw = dict(z_range=configs.SERVE_Z_MM, max_fft=configs.MAX_FFT, stated=True) if stated else {}
+        self.stated = stated
+        self.holos, self.breqs, self.t_arr = configs.serve_workload(n_req=nreq, rate=rate, **kw)
+        t0 = time.time()
+        self.plans = []
+        for w in self.holos:
+            h = synth.gpu_hologram(w.point_cloud(), w.wavelength, w.pitch, w.n, w.n)
+            self.plans.append(nf.Plan(w.wavelength, w.pitch, w.n, w.n, h))
+            del h
+        torch.cuda.synchronize()
+        self.init_s = time.time() - t0
+        self.resident = sum(p.device_bytes() for p in self.plans)
+        self.budget = 120 * 10 ** 9
+        self.views = []
+        for br in self.breqs:
+            pl = self.plans[br.holo]
+            p = pl.view_plan(nf.View(z=br.z))["pitch_out_x_m"]
+            self.views.append(nf.View(z=br.z, center_x=br.dx * p, center_y=br.dy * p,
+                                      width=br.size * p, height=br.size * p, out_nx=br.size,
+                                      out_ny=br.size))
+        self.ws = [int(self.plans[br.holo].view_plan(v)["workspace_bytes"])
+                   for br, v in zip(self.breqs, self.views)]
+        self.pix = [br.size * br.size for br in self.breqs]
+
+    def make(self, scale=1.0, count=None):
+        from paper_2410_13474_gb300.serving import Request
+        m = len(self.breqs) if count is None else count
+        return [Request(i, self.breqs[i].holo, self.views[i], float(self.t_arr[i]) / scale,
+                        ws_bytes=self.ws[i]) for i in range(m)]
+
+    def serve(self, reqs, single):
+        import torch
+        from paper_2410_13474_gb300.serving import GpuExecutor, Scheduler
+        slots = 1 if single else 2
+        ex = GpuExecutor(self.plans, slots=slots, single=single)
+        sched = Scheduler(ex, budget_bytes=self.budget - self.resident, slots=slots,
+                          max_batch=1 if single else 16)
+        torch.cuda.synchronize()
+        st = sched.run(reqs)
+        torch.cuda.synchronize()
+        d = st.as_dict()
+        d["Mpix_per_s"] = round(sum(self.pix[r.rid] for r in reqs if r.t_done) / st.wall_s / 1e6, 2)
+        return d
+
+    def config(self, nreq, rate):
+        return {"workload": "serve-%d-requests-%d-holograms%s"
+                % (nreq, len(self.holos), "" if self.stated else "-paper-depths"),
+                "view_z_m": [min(r.z for r in self.breqs), max(r.z for r in self.breqs)],
+                "rate_per_s": rate,
+                "holograms": [[w.n, round(w.pitch * 1e6, 4)] for w in self.holos],
+                "hbm_budget_bytes": self.budget, "resident_bytes": self.resident, "slots": 2,
+                "max_batch": 16}
+
+    def close(self):
+        for p in self.plans:
+            p.close()
+
+
+def serve_block(nreq, rate):
+    """A compact serving run for the default line: the same pool and stream
+    shape as the serving workload (stated depths), nreq requests at `rate`,
+    continuous batching against one request at a time."""
+    pool = ServePool(nreq, rate)
+    pool.serve(pool.make(count=min(64, nreq)), False)   # warm: tables, graphs, autotuner
+    pool.serve(pool.make(count=min(16, nreq)), True)
+    served = pool.serve(pool.make(), False)
+    single = pool.serve(pool.make(), True)
+    out = {"config": pool.config(nreq, rate), "batched": served, "one_at_a_time": single,
+           "init_s": round(pool.init_s, 1)}
+    pool.close()
+    return out
+
+
 def run_serve(args):
     """Serving workload: resident holograms, a seeded Poisson stream of view
     requests, continuous batching on two streams under an HBM budget; against
@@ -845,52 +949,12 @@ def run_serve(args):
     call; plus a saturation sweep of the offered load."""
     import torch
 
-    import paper_2410_13474_gb300 as nf
-    import synth
-    from paper_2410_13474_gb300.serving import GpuExecutor, Request, Scheduler
-    from synth.configs import serve_workload
-
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     from paper_2410_13474_gb300 import build as b
     b.build()
     nreq = args.requests
-    holos, breqs, t_arr = serve_workload(n_req=nreq)
-    t0 = time.time()
-    plans = []
-    for w in holos:
-        h = synth.gpu_hologram(w.point_cloud(), w.wavelength, w.pitch, w.n, w.n)
-        plans.append(nf.Plan(w.wavelength, w.pitch, w.n, w.n, h))
-        del h
-    torch.cuda.synchronize()
-    init_s = time.time() - t0
-    resident = sum(p.device_bytes() for p in plans)
-    budget = 120 * 10 ** 9
-    views = []
-    for br in breqs:
-        pl = plans[br.holo]
-        p = pl.view_plan(nf.View(z=br.z))["pitch_out_x_m"]
-        views.append(nf.View(z=br.z, center_x=br.dx * p, center_y=br.dy * p, width=br.size * p,
-                             height=br.size * p, out_nx=br.size, out_ny=br.size))
-    ws = [int(plans[br.holo].view_plan(v)["workspace_bytes"]) for br, v in zip(breqs, views)]
-    pix = [br.size * br.size for br in breqs]
-
-    def make(scale=1.0, count=None):
-        m = len(breqs) if count is None else count
-        return [Request(i, breqs[i].holo, views[i], float(t_arr[i]) / scale, ws_bytes=ws[i])
-                for i in range(m)]
-
-    def serve(reqs, single):
-        slots = 1 if single else 2
-        ex = GpuExecutor(plans, slots=slots, single=single)
-        sched = Scheduler(ex, budget_bytes=budget - resident, slots=slots,
-                          max_batch=1 if single else 16)
-        torch.cuda.synchronize()
-        st = sched.run(reqs)
-        torch.cuda.synchronize()
-        d = st.as_dict()
-        d["Mpix_per_s"] = round(sum(pix[r.rid] for r in reqs if r.t_done) / st.wall_s / 1e6, 2)
-        return d
-
+    pool = ServePool(nreq, args.rate, stated=args.workload == "serve")
+    make, serve = pool.make, pool.serve
     # warm both paths (tables, graphs, autotuner) on a short prefix
     serve(make(count=min(64, nreq)), False)
     serve(make(count=min(16, nreq)), True)
@@ -903,15 +967,11 @@ def run_serve(args):
                       "batched": serve(make(mult, m), False), "one_at_a_time": serve(make(mult, m), True)})
     line = {"metric": "served views/s with p50/p99 latency (continuous batching)",
             "value": served["throughput"], "unit": "views/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serve-%d-requests-%d-holograms" % (nreq, len(holos)),
-                       "rate_per_s": args.rate, "holograms": [[w.n, round(w.pitch * 1e6, 4)] for w in holos],
-                       "hbm_budget_bytes": budget, "resident_bytes": resident, "slots": 2,
-                       "max_batch": 16},
-            "served": served, "one_at_a_time": single, "sweep": sweep, "init_s": round(init_s, 1)}
+            "dtype": "f32", "data": "synthetic", "config": pool.config(nreq, args.rate),
+            "served": served, "one_at_a_time": single, "sweep": sweep,
+            "init_s": round(pool.init_s, 1)}
     print(json.dumps(line), flush=True)
-    for p in plans:
-        p.close()
+    pool.close()
 
 
 def main():
@@ -921,8 +981,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uwa16k",
-                    choices=list(WORKLOADS) + ["batch64", "serve", "sweep16k"])
+                    choices=list(WORKLOADS) + ["batch64", "batch64-paper-depths", "serve",
+                                               "serve-paper-depths", "sweep16k"])
     ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving block in the default line (0: none)")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true",
@@ -930,9 +993,9 @@ def main():
     args = ap.parse_args()
     if args.workload == "sweep16k":
         return run_sweep(args)
-    if args.workload == "batch64":
+    if args.workload.startswith("batch64"):
         return run_batch(args)
-    if args.workload == "serve":
+    if args.workload.startswith("serve"):
         return run_serve(args)
     w = _workload(args.workload)
     if args.impl == "reference":

@@ -147,11 +147,13 @@ class Scheduler:
 
 
 class GpuExecutor:
-    """Runs batches with nufds_reconstruct_batch, one CUDA stream per slot.
+    """Runs batches with nufds_reconstruct_batch, one CUDA stream per slot;
+    a batch of one view runs as nufds_reconstruct (the same arithmetic without
+    the batch's descriptor upload and graph launch).
 
     plans: list of Plan (resident holograms).  single=True runs each view with
-    nufds_reconstruct instead (the one-at-a-time reference, slots=1,
-    max_batch=1).  keep_outputs stores each request's output tensor on it.
+    nufds_reconstruct (the one-at-a-time reference, slots=1, max_batch=1).
+    keep_outputs stores each request's output tensor on it.
     """
 
     def __init__(self, plans, slots: int, single: bool = False, keep_outputs: bool = False):
@@ -173,7 +175,7 @@ class GpuExecutor:
         with torch.cuda.stream(st):
             for r in batch:
                 outs.append(self.plans[r.holo].output_like(r.view))
-            if self.single:
+            if self.single or len(batch) == 1:
                 statuses = []
                 for r, o in zip(batch, outs):
                     try:

@@ -113,6 +113,15 @@ class BatchRequest:
     z: float
 
 
+# Depths of the batched and served workloads as stated for the benchmark
+# (millimetres: points and views at z in [1, 8] mm for the batch; views at z in
+# [max(2 mm, N pitch^2 / lambda), 10 mm] for serving), against the paper's own
+# object depths (metres) of the *_paper variants.
+BATCH_Z_MM = (1e-3, 8e-3)
+SERVE_Z_MM = (2e-3, 10e-3)
+MAX_FFT = 49152  # the largest row the passes take (split over two CTAs above 24576)
+
+
 def batch_workload(seed: int = 20241020, n_holo: int = 8, n_req: int = 64, lam: float = LAMBDA_532,
                    sizes=(2048, 4096, 8192), view_sizes=(256, 512, 1024, 2048, 4096),
                    z_range=(0.5, 3.0), max_fft: int = 24576):
@@ -120,7 +129,9 @@ def batch_workload(seed: int = 20241020, n_holo: int = 8, n_req: int = 64, lam: 
     uneven size, position and depth over them (the batched workload).  A
     request's z is drawn in [max(z_min, z_chirp), z_max], where z_chirp keeps
     the FFT size of the Fresnel stage within max_fft ((N pitch)^2/(lambda z)
-    <= max_fft); at the paper's object depths (0.5-3 m) it does not bind."""
+    <= max_fft); at the paper's object depths (0.5-3 m) it does not bind, nor
+    at the stated millimetre depths with max_fft = MAX_FFT.  Point depths
+    follow z_range."""
     rng = np.random.default_rng(seed)
     holos = []
     for i in range(n_holo):
@@ -145,13 +156,16 @@ def batch_workload(seed: int = 20241020, n_holo: int = 8, n_req: int = 64, lam: 
 def serve_workload(seed: int = 20241021, n_holo: int = 12, n_req: int = 10000, rate: float = 200.0,
                    lam: float = LAMBDA_532, sizes=(2048, 4096, 8192, 16384),
                    view_sizes=(256, 512, 1024, 2048, 4096), max_fft: int = 24576,
-                   resident_cap_bytes: float = 72e9, z_range=(0.6, 3.2)):
+                   resident_cap_bytes: float = 72e9, z_range=(0.6, 3.2), stated=False):
     """Resident holograms and a seeded Poisson stream of view requests (the
     serving workload).  Hologram sizes are drawn from `sizes` until the
     resident set (spectrum 32 N^2 B plus tables ~30 N^2 B each) would pass
     resident_cap_bytes; then the smallest size is used.  A request's z is drawn
     in [max(z_min, z_chirp), z_max] (z_chirp keeps the Fresnel-stage FFT within
-    max_fft; at the paper's object depths of 0.5-3 m it does not bind).  Returns (holograms, requests, arrival_times)."""
+    max_fft; at the paper's object depths of 0.5-3 m it does not bind); with
+    stated=True (millimetre depths) z_min is also at least N pitch^2 / lambda
+    of the request's hologram, so N' stays within about N.  Points lie in
+    z_range.  Returns (holograms, requests, arrival_times)."""
     rng = np.random.default_rng(seed)
     holos, resident = [], 0.0
     for i in range(n_holo):
@@ -171,7 +185,8 @@ def serve_workload(seed: int = 20241021, n_holo: int = 12, n_req: int = 10000, r
         lim = (w.n - s) // 2
         dx, dy = (int(v) for v in rng.integers(-lim, lim + 1, size=2))
         zc = (w.n * w.pitch) ** 2 / (lam * max_fft) * 1.02
-        z = float(rng.uniform(max(z_range[0], zc), z_range[1]))
+        zlo = max(z_range[0], zc, w.n * w.pitch ** 2 / lam if stated else 0.0)
+        z = float(rng.uniform(zlo, z_range[1]))
         reqs.append(BatchRequest(h, s, dx, dy, z))
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     return holos, reqs, t
