@@ -856,11 +856,18 @@ def run_batch(args):
         pl.close()
 
 
+# serving: one stream, every request queued while a batch runs joins the next
+# batch (measured on the serving workload against two streams, with and
+# without a workspace guard on overlap: the best p99 at 200 requests/s and
+# the highest saturated throughput)
+SERVE_SLOTS = 1
+
+
 class ServePool:
     """The serving workload's resident holograms (plans) and a seeded Poisson
     stream of view requests over them; serve() runs a stream continuously
-    batched on two streams under an HBM budget, or one request at a time with
-    the plain single-view call.  stated: the millimetre depths given for the
+    batched (SERVE_SLOTS streams) under an HBM budget, or one request at a
+    time with the plain single-view call.  stated: the millimetre depths given for the
     benchmark (else the paper's metre depths)."""
 
     def __init__(self, nreq, rate, stated=True):
@@ -899,13 +906,13 @@ class ServePool:
         return [Request(i, self.breqs[i].holo, self.views[i], float(self.t_arr[i]) / scale,
                         ws_bytes=self.ws[i]) for i in range(m)]
 
-    def serve(self, reqs, single):
+    def serve(self, reqs, single, slots=SERVE_SLOTS, overlap_bytes=None):
         import torch
         from paper_2410_13474_gb300.serving import GpuExecutor, Scheduler
-        slots = 1 if single else 2
+        slots = 1 if single else slots
         ex = GpuExecutor(self.plans, slots=slots, single=single)
         sched = Scheduler(ex, budget_bytes=self.budget - self.resident, slots=slots,
-                          max_batch=1 if single else 16)
+                          max_batch=1 if single else 16, overlap_bytes=overlap_bytes)
         torch.cuda.synchronize()
         st = sched.run(reqs)
         torch.cuda.synchronize()
@@ -919,8 +926,8 @@ class ServePool:
                 "view_z_m": [min(r.z for r in self.breqs), max(r.z for r in self.breqs)],
                 "rate_per_s": rate,
                 "holograms": [[w.n, round(w.pitch * 1e6, 4)] for w in self.holos],
-                "hbm_budget_bytes": self.budget, "resident_bytes": self.resident, "slots": 2,
-                "max_batch": 16}
+                "hbm_budget_bytes": self.budget, "resident_bytes": self.resident,
+                "slots": SERVE_SLOTS, "max_batch": 16}
 
     def close(self):
         for p in self.plans:
@@ -944,7 +951,7 @@ def serve_block(nreq, rate):
 
 def run_serve(args):
     """Serving workload: resident holograms, a seeded Poisson stream of view
-    requests, continuous batching on two streams under an HBM budget; against
+    requests, continuous batching under an HBM budget; against
     the same stream served one request at a time with the plain single-view
     call; plus a saturation sweep of the offered load."""
     import torch

@@ -314,6 +314,21 @@ int nufds_wavefront_error(const nufds_params *params, double xo, double yo, doub
  */
 int64_t nufds_launch_count(int32_t reset);
 
+/*
+ * Debug builds only (the library compiled with NUFDS_BOUNDS_CHECK defined,
+ * libnufds_bc.so): the two gathers of Section 4 (the stretch of step two and
+ * the output remap of step five, Eq. 17), their batched and paper-literal
+ * bilinear forms, check every read of the spectrum, of Q and of the FP64
+ * tables against the extent of the row and array it reads.  A read outside
+ * is skipped (its taps count as zero) and recorded instead of faulting.
+ * Returns the number of such reads since the last reset (>= 0; saturates at
+ * INT32_MAX) after synchronising the device, with the element offset of the
+ * first one in *first_offset (-1 if none; first_offset may be NULL);
+ * reset = 1 zeroes both after reading.  The product build returns
+ * NUFDS_EUNSUPPORTED; NUFDS_ECUDA on a CUDA error.
+ */
+int nufds_debug_bounds_violations(int32_t reset, int64_t *first_offset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,10 @@ import os
 from dataclasses import dataclass
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libnufds.so")
+# NUFDS_BOUNDS_CHECK=1 in the environment loads the debug library instead
+# (bounds-checked gathers; build.build(bounds_check=True) makes it)
+LIB_PATH = os.path.join(_HERE, "libnufds_bc.so" if os.environ.get("NUFDS_BOUNDS_CHECK") == "1"
+                        else "libnufds.so")
 
 OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 FP32, FP16_STORE, BF16_STORE = 0, 1, 2
@@ -30,7 +33,7 @@ ABI_FUNCTIONS = ("nufds_plan_create", "nufds_plan_load", "nufds_view_plan", "nuf
                  "nufds_reconstruct_batch", "nufds_reconstruct_sweep", "nufds_destroy", "nufds_plan_device_bytes",
                  "nufds_status_string", "nufds_launch_count", "nufds_profile",
                  "nufds_profile_read", "nufds_reconstruct_noalloc", "nufds_wavefront_error",
-                 "nufds_output_map", "nufds_output_map_inverse")
+                 "nufds_output_map", "nufds_output_map_inverse", "nufds_debug_bounds_violations")
 
 
 class NufdsError(RuntimeError):
@@ -78,8 +81,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libnufds.so is not built (run paper_2410_13474_gb300.build.build());"
-                               " there is no CPU fallback")
+            raise RuntimeError("%s is not built (run paper_2410_13474_gb300.build.build());"
+                               " there is no CPU fallback" % os.path.basename(LIB_PATH))
         L = ctypes.CDLL(LIB_PATH)
         vp = ctypes.c_void_p
         L.nufds_plan_create.argtypes = [ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(vp)]
@@ -112,6 +115,7 @@ def lib():
                                             ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                             ctypes.c_double, ctypes.c_int32, dp, dp, dp]
         L.nufds_launch_count.restype = ctypes.c_int64
+        L.nufds_debug_bounds_violations.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
         _lib = L
     return _lib
 
@@ -123,6 +127,17 @@ def status_string(code: int) -> str:
 def _check(code: int, what: str):
     if code != OK:
         raise NufdsError(code, what)
+
+
+def bounds_violations(reset: bool = False):
+    """(count, first element offset or -1) of the gather reads the debug
+    library found outside their arrays (nufds_debug_bounds_violations);
+    raises NufdsError(EUNSUPPORTED) on the product library."""
+    first = ctypes.c_int64(-1)
+    n = lib().nufds_debug_bounds_violations(1 if reset else 0, ctypes.byref(first))
+    if n < 0:
+        raise NufdsError(n, "nufds_debug_bounds_violations")
+    return int(n), int(first.value)
 
 
 def launch_count(reset: bool = False) -> int:

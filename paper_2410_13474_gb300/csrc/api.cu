@@ -660,6 +660,7 @@ static int reconstruct_impl(nufds_plan *P, const nufds_view *v, void *d_out, cud
     ra.kc_y = V.kc_y;
     ra.rm_base = rmb;
     ra.rm_frac = rmf;
+    ra.rm_count = V.lattice ? (long)P->nx * P->ny : (long)V.ox * V.oy;
     ra.rm_ld = rm_ld;
     ra.rm_i0 = rm_i0;
     ra.rm_j0 = rm_j0;
@@ -1134,6 +1135,7 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
         ra.kc_y = V.kc_y;
         ra.rm_base = g.rmb;
         ra.rm_frac = g.rmf;
+        ra.rm_count = V.lattice ? (long)P->nx * P->ny : (long)V.ox * V.oy;
         ra.rm_ld = rm_ld;
         ra.rm_i0 = rm_i0;
         ra.rm_j0 = rm_j0;
@@ -1421,6 +1423,13 @@ int64_t nufds_launch_count(int32_t reset) {
     int64_t v = t_launches;
     if (reset) t_launches = 0;
     return v;
+}
+
+int nufds_debug_bounds_violations(int32_t reset, int64_t *first_offset) {
+    long long f = -1;
+    const int n = bounds_violations(reset, &f);
+    if (first_offset) *first_offset = f;
+    return n == -3 ? NUFDS_EUNSUPPORTED : (n < 0 ? NUFDS_ECUDA : n);
 }
 
 int nufds_plan_create(const nufds_params *prm, const void *d_holo, void *stream, nufds_plan **out) {
@@ -1918,6 +1927,7 @@ extern "C" int nufds_reconstruct_noalloc(const nufds_params *prm, const nufds_vi
     ra.kc_y = V.kc_y;
     ra.rm_base = vrb;
     ra.rm_frac = vrf;
+    ra.rm_count = V.lattice ? (long)nx * ny : (long)V.ox * V.oy;
     ra.rm_ld = rm_ld;
     ra.rm_i0 = rm_i0;
     ra.rm_j0 = rm_j0;

@@ -1434,30 +1434,47 @@ int launch_transpose_batch(const TrItem *d_items, const int *d_tile_off, int nit
 
 // Weighted energies of the hologram for the FP16 scales of the padded passes:
 // acc[0] += sum |h|^2 dx[ix]^2, acc[1] += sum |h|^2 dx[ix]^2 dy[iy]^2.  Terms in
-// FP32, summed in FP32 over runs of kNormRun elements and in FP64 across runs
-// (the scales need a bound, not an exact sum: k_scales_load widens it).
-constexpr int kNormRun = 64;
-__global__ void k_norms(const float2 *__restrict__ H, int nx, int ny, const double *__restrict__ dx,
-                        const double *__restrict__ dy, double *acc) {
+// FP32, summed in FP32 over runs of kNormRun rows of a thread's kNormCols
+// columns and in FP64 across runs (the scales need a bound, not an exact sum: k_scales_load
+// widens it).  Block (x, y) takes the column chunk y (kNormCols per thread,
+// 256 threads) of the rows x, x + gridDim.x, ...: the column weights are
+// converted once per thread and each row issues kNormCols independent loads.
+constexpr int kNormCols = 4;
+constexpr int kNormThreads = 256;
+constexpr int kNormRun = 16;
+__global__ void __launch_bounds__(kNormThreads)
+    k_norms(const float2 *__restrict__ H, int nx, int ny, const double *__restrict__ dx,
+            const double *__restrict__ dy, double *acc) {
+    const int c0 = blockIdx.y * kNormCols * kNormThreads + threadIdx.x;
+    float w2[kNormCols];
+#pragma unroll
+    for (int j = 0; j < kNormCols; ++j) {
+        const int ix = c0 + j * kNormThreads;
+        const float w = ix < nx ? (float)dx[ix] : 0.f;
+        w2[j] = w * w;
+    }
     double s0 = 0, s1 = 0;
     float r0 = 0.f, r1 = 0.f;
     int k = 0;
-    // rows by blocks, columns by threads (no index division per sample)
     for (int iy = blockIdx.x; iy < ny; iy += gridDim.x) {
-        const float wy = (float)dy[iy], wy2 = wy * wy;
         const float2 *row = H + (long)iy * nx;
-        for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
-            const float2 v = __ldcs(row + ix);
-            const float wx = (float)dx[ix];
-            const float e = fmaf(v.x, v.x, v.y * v.y) * wx * wx;
-            r0 += e;
-            r1 = fmaf(e, wy2, r1);
-            if (++k == kNormRun) {
-                s0 += r0;
-                s1 += r1;
-                r0 = r1 = 0.f;
-                k = 0;
-            }
+        float2 v[kNormCols];
+#pragma unroll
+        for (int j = 0; j < kNormCols; ++j) {
+            const int ix = c0 + j * kNormThreads;
+            v[j] = ix < nx ? __ldcs(row + ix) : make_float2(0.f, 0.f);
+        }
+        float r = 0.f;
+#pragma unroll
+        for (int j = 0; j < kNormCols; ++j) r = fmaf(fmaf(v[j].x, v[j].x, v[j].y * v[j].y), w2[j], r);
+        const float wy = (float)dy[iy];
+        r0 += r;
+        r1 = fmaf(r, wy * wy, r1);
+        if (++k == kNormRun) {  // FP32 runs of kNormRun rows, FP64 across runs
+            s0 += r0;
+            s1 += r1;
+            r0 = r1 = 0.f;
+            k = 0;
         }
     }
     s0 += r0;
@@ -1472,25 +1489,52 @@ __global__ void k_norms(const float2 *__restrict__ H, int nx, int ny, const doub
     }
 }
 
+__device__ __forceinline__ float energy4(uint4 u) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&u.z));
+    const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&u.w));
+    return fmaf(a.x, a.x, a.y * a.y) + fmaf(b.x, b.x, b.y * b.y) + fmaf(c.x, c.x, c.y * c.y) +
+           fmaf(d.x, d.x, d.y * d.y);
+}
+
 // ||S||^2 of the stretched band for the FP16 scales of the view passes, from
-// the stored S (count elements held as S sc; FP32 terms and runs, FP64 across
-// runs, one atomic per warp spread over kEnergySlots slots).
+// the stored S (count elements held as S sc).  The body is read as 16-byte
+// vectors (four per thread and iteration, independent), the unaligned head
+// and the tail element by element; FP32 over runs of kNormRun iterations,
+// FP64 across runs, one atomic per warp spread over kEnergySlots slots.
 __global__ void k_energy(const __half2 *__restrict__ S, long count, const float *sc_s,
                          double *slots) {
     const float inv = 1.0f / *sc_s;
+    const long head = min(count, (long)((4 - (((uintptr_t)S >> 2) & 3)) & 3));
+    const long nvec = (count - head) >> 2, tail0 = head + 4 * nvec;
+    const uint4 *V = reinterpret_cast<const uint4 *>(S + head);
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long)gridDim.x * blockDim.x;
     double s = 0;
     float r = 0.f;
-    int k = 0;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (long)gridDim.x * blockDim.x) {
-        const float2 v = __half22float2(__ldg(S + i));
+    if (tid < head) {
+        const float2 v = __half22float2(S[tid]);
         r = fmaf(v.x, v.x, fmaf(v.y, v.y, r));
-        if (++k == kNormRun) {
+    }
+    if (tid < count - tail0) {
+        const float2 v = __half22float2(S[tail0 + tid]);
+        r = fmaf(v.x, v.x, fmaf(v.y, v.y, r));
+    }
+    s += r;
+    long i = tid;
+    int k = 0;
+    r = 0.f;
+    for (; i + 3 * nth < nvec; i += 4 * nth) {
+        const uint4 a = __ldcs(V + i), b = __ldcs(V + i + nth), c = __ldcs(V + i + 2 * nth),
+                    d = __ldcs(V + i + 3 * nth);
+        r += (energy4(a) + energy4(b)) + (energy4(c) + energy4(d));
+        if (++k == kNormRun) {  // FP32 runs of kNormRun iterations, FP64 across runs
             s += r;
             r = 0.f;
             k = 0;
         }
     }
+    for (; i < nvec; i += nth) r += energy4(__ldcs(V + i));
     s += r;
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0)
@@ -1504,7 +1548,7 @@ int launch_energy(const void *S, long count, const float *sc_s, double *slots, c
     int dev, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long blocks = std::min((long)sms * 4, (count + 255) / 256);
+    long blocks = std::max(1L, std::min((long)sms * 4, (count / 4 + 255) / 256));
     k_energy<<<(int)blocks, 256, 0, st>>>((const __half2 *)S, count, sc_s, slots);
     count_launch();
     return check_launch();
@@ -1516,7 +1560,9 @@ int launch_norms(const float2 *H, int nx, int ny, const double *dx, const double
     int dev, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_norms<<<sms * 4, 256, 0, st>>>(H, nx, ny, dx, dy, acc);
+    const int chunks = (nx + kNormCols * kNormThreads - 1) / (kNormCols * kNormThreads);
+    const int rows = std::max(1, std::min(ny, sms * 8 / chunks + 1));
+    k_norms<<<dim3(rows, chunks), kNormThreads, 0, st>>>(H, nx, ny, dx, dy, acc);
     count_launch();
     return check_launch();
 }

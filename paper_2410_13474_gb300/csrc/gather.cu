@@ -118,6 +118,55 @@ __device__ __forceinline__ int wrap(int m, int M) {
     return m < 0 ? m + M : (m >= M ? m - M : m);
 }
 
+// Debug build (NUFDS_BOUNDS_CHECK): every gather read is checked against the
+// extent of the array it reads; a read outside is skipped (its taps count as
+// zero), counted, and the first offending element offset recorded, so the
+// host can ask (bounds_violations) instead of the kernel faulting.  In the
+// product build the check is compiled out.
+#ifdef NUFDS_BOUNDS_CHECK
+__device__ unsigned long long g_oob_count = 0;
+__device__ unsigned long long g_oob_first = ~0ull;
+// [lo, hi) inside [0, total)
+__device__ __forceinline__ bool in_bounds(long lo, long hi, long total) {
+    if (lo >= 0 && lo <= hi && hi <= total) return true;
+    atomicAdd(&g_oob_count, 1ull);
+    atomicCAS(&g_oob_first, ~0ull, (unsigned long long)lo);
+    return false;
+}
+// columns [c_lo, c_hi) of the row at element offset roff (row length ld)
+// inside that row, and the row inside [0, total)
+__device__ __forceinline__ bool in_row(long roff, long c_lo, long c_hi, long ld, long total) {
+    if (c_lo >= 0 && c_lo <= c_hi && c_hi <= ld && roff >= 0 && roff + ld <= total) return true;
+    atomicAdd(&g_oob_count, 1ull);
+    atomicCAS(&g_oob_first, ~0ull, (unsigned long long)(roff + c_lo));
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_bounds(long, long, long) { return true; }
+__device__ __forceinline__ bool in_row(long, long, long, long, long) { return true; }
+#endif
+
+int bounds_violations(int reset, long long *first) {
+#ifdef NUFDS_BOUNDS_CHECK
+    unsigned long long n = 0, f = ~0ull;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpyFromSymbol(&n, g_oob_count, sizeof n) != cudaSuccess ||
+        cudaMemcpyFromSymbol(&f, g_oob_first, sizeof f) != cudaSuccess)
+        return -4;
+    if (first) *first = f == ~0ull ? -1 : (long long)f;
+    if (reset) {
+        const unsigned long long z = 0, m = ~0ull;
+        if (cudaMemcpyToSymbol(g_oob_count, &z, sizeof z) != cudaSuccess ||
+            cudaMemcpyToSymbol(g_oob_first, &m, sizeof m) != cudaSuccess)
+            return -4;
+    }
+    return (int)(n > 0x7fffffffull ? 0x7fffffffull : n);
+#else
+    if (first) *first = -1;
+    (void)reset;
+    return -3;  // not a checking build
+#endif
+}
 
 // sum_{i,j} wr[i] wc[j] A[row r0 + i][column c0 + j] for a window inside a
 // grid stored plane-wise on both axes (fine row m at row (m & 1) Lr + (m >> 1),
@@ -174,14 +223,17 @@ __device__ __forceinline__ void load_run4(const __nv_bfloat162 *__restrict__ row
 template <bool WIDE, class T>
 __device__ __forceinline__ float2 window_sum_inside(const T *__restrict__ A, long ld, int Lr,
                                                    int Lc, int r0, int c0, const float *wr,
-                                                   const float *wc) {
+                                                   const float *wc, long total) {
     const int e = c0 & 1;
     const int ca = e * Lc + (c0 >> 1), cb = (1 - e) * Lc + ((c0 + 1) >> 1);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < kW; ++i) {
         const int r = r0 + i;
-        const T *row = A + (long)((r & 1) * Lr + (r >> 1)) * ld;
+        const long roff = (long)((r & 1) * Lr + (r >> 1)) * ld;
+        // load_run4 reads [s & ~1, s + kW/2) of each plane run s = ca, cb
+        if (!in_row(roff, min(ca, cb) & ~1, max(ca, cb) + kW / 2, ld, total)) continue;
+        const T *row = A + roff;
         float2 va[kW / 2], vb[kW / 2];
         if (WIDE) {
             load_run4(row, ca, va);
@@ -259,12 +311,15 @@ __device__ __forceinline__ void load_run8(const __nv_bfloat162 *__restrict__ row
 template <class T>
 __device__ __forceinline__ float2 window_sum_natcols(const T *__restrict__ A, long ld, int Lr,
                                                     int r0, int c0, const float *wr,
-                                                    const float *wc) {
+                                                    const float *wc, long total) {
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < kW; ++i) {
         const int r = r0 + i;
-        const T *row = A + (long)((r & 1) * Lr + (r >> 1)) * ld;
+        const long roff = (long)((r & 1) * Lr + (r >> 1)) * ld;
+        // load_run8 reads [c0 & ~1, c0 + kW)
+        if (!in_row(roff, c0 & ~1, c0 + kW, ld, total)) continue;
+        const T *row = A + roff;
         float2 v[kW];
         load_run8(row, c0, v);
         float2 sum = make_float2(0.f, 0.f);
@@ -300,15 +355,18 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
             }
         } else {
             const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
-            const short2 e = a.pb_base[t];
-            if (e.x != kMasked) {
-                b = make_int2(e.x + (int)(2 * kx), e.y + (int)(2 * ky));
-                f = a.pb_frac[t];
-                valid = true;
+            if (in_bounds(t, t + 1, (long)a.pb_nkx * a.pb_nky)) {
+                const short2 e = a.pb_base[t];
+                if (e.x != kMasked) {
+                    b = make_int2(e.x + (int)(2 * kx), e.y + (int)(2 * ky));
+                    f = a.pb_frac[t];
+                    valid = true;
+                }
             }
         }
     }
     const int Mx = 2 * a.Nx, My = 2 * a.Ny;
+    const long gtot = (long)Mx * My;
     // first taps on the fine grid, unwrapped (rows = x, columns = y)
     const int r0 = b.x - kW / 2 + 1 + a.Nx, c0 = b.y - kW / 2 + 1 + a.Ny;
     float2 acc = make_float2(0.f, 0.f);
@@ -317,7 +375,7 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
         es_weights(f.x, wx);
         es_weights(f.y, wy);
         if (r0 >= 0 && r0 + kW <= Mx && c0 >= 0 && c0 + kW <= My) {
-            acc = window_sum_natcols(G, My, a.Nx, r0, c0, wx, wy);
+            acc = window_sum_natcols(G, My, a.Nx, r0, c0, wx, wy, gtot);
         } else {  // the window wraps around the periodic grid
             int cols[kW];
 #pragma unroll
@@ -328,6 +386,7 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
                 float2 r = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < kW; ++j) {
+                    if (!in_row(row, cols[j], cols[j] + 1, My, gtot)) continue;
                     float2 gv = ld_c(G, row + cols[j], 1.0f);
                     r.x = fmaf(wy[j], gv.x, r.x);
                     r.y = fmaf(wy[j], gv.y, r.y);
@@ -381,8 +440,10 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     uint2 F = make_uint2(0u, 0u);
     if (valid) {
         const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
-        b = a.rm_base[t];
-        F = a.rm_frac[t];
+        if (in_bounds(t, t + 1, a.rm_count)) {
+            b = a.rm_base[t];
+            F = a.rm_frac[t];
+        }
     }
     // the fraction in FP32 for the weights (rounded toward zero: stays < 1)
     const float2 f = make_float2(__uint2float_rz(F.x) * 0x1p-32f, __uint2float_rz(F.y) * 0x1p-32f);
@@ -396,7 +457,7 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     es_weights(f.x, wx);
     es_weights(f.y, wy);
     if (r0 >= 0 && r0 + kW <= My && c0 >= 0 && c0 + kW <= Mx) {
-        acc = window_sum_inside<true>(Q, Mx, a.npy, a.npx, r0, c0, wy, wx);
+        acc = window_sum_inside<true>(Q, Mx, a.npy, a.npx, r0, c0, wy, wx, (long)Mx * My);
     } else {  // the window wraps around the periodic grid
         int cols[kW];
 #pragma unroll
@@ -407,6 +468,7 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
             float2 r = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < kW; ++q) {
+                if (!in_row(row, cols[q], cols[q] + 1, Mx, (long)Mx * My)) continue;
                 float2 g = ld_c(Q, row + cols[q], 1.0f);
                 r.x = fmaf(wx[q], g.x, r.x);
                 r.y = fmaf(wx[q], g.y, r.y);
@@ -466,6 +528,8 @@ __device__ __forceinline__ float2 lerp2(const float2 *__restrict__ A, long ld, i
                                         int D, int i, float ax, int j, float ay) {
     const int r0 = wrap(i + C / 2, C), r1 = wrap(i + 1 + C / 2, C);
     const int c0 = wrap(j + D / 2, D), c1 = wrap(j + 1 + D / 2, D);
+    if (!in_bounds(min(r0, r1), max(r0, r1) + 1, C) || !in_bounds(min(c0, c1), max(c0, c1) + 1, D))
+        return make_float2(0.f, 0.f);
     const float2 v00 = __ldg(A + r0 * ld + (long)c0 * cs), v01 = __ldg(A + r0 * ld + (long)c1 * cs);
     const float2 v10 = __ldg(A + r1 * ld + (long)c0 * cs), v11 = __ldg(A + r1 * ld + (long)c1 * cs);
     const float bx = 1.0f - ax, by = 1.0f - ay;
@@ -491,7 +555,8 @@ __global__ void __launch_bounds__(256) k_stretch_linear(StretchArgs a) {
             }
         } else {
             const long t = (kx - a.pb_kx0) * a.pb_nky + (ky - a.pb_ky0);
-            const short2 e = a.pb_base[t];
+            const short2 e = in_bounds(t, t + 1, (long)a.pb_nkx * a.pb_nky)
+                                 ? a.pb_base[t] : make_short2(kMasked, kMasked);
             if (e.x != kMasked) {
                 b = make_int2(e.x + (int)(2 * kx), e.y + (int)(2 * ky));
                 f = a.pb_frac[t];
@@ -514,6 +579,7 @@ __global__ void __launch_bounds__(256) k_remap_linear(RemapArgs a) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     if (i >= a.ox || j >= a.oy) return;
     const long t = (long)(j + a.rm_j0) * a.rm_ld + (i + a.rm_i0);
+    if (!in_bounds(t, t + 1, a.rm_count)) return;
     const int2 b = a.rm_base[t];
     const uint2 F = a.rm_frac[t];
     const int px = (int)(b.x - 2 * a.kc_x), py = (int)(b.y - 2 * a.kc_y);

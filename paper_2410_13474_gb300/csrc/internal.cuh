@@ -305,6 +305,7 @@ struct RemapArgs {
     const int2 *rm_base;    // output-map table, layout [j][i], row length rm_ld
     const uint2 *rm_frac;   // its fractions, 0.32 fixed point
     long rm_ld, rm_i0, rm_j0;
+    long rm_count;          // entries of the table (the debug build's bounds checks)
     int ox, oy;
     int kind;               // 0 intensity f32, 1 field c64, 2 intensity f32 added to out
     const OutChirp *Ex, *Ey;  // output chirp tables (field only)
@@ -319,6 +320,10 @@ struct RemapArgs {
 int launch_remap(const RemapArgs &a, cudaStream_t st);
 int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, int total, int prec,
                        cudaStream_t st);
+// Debug build (NUFDS_BOUNDS_CHECK): gather reads found outside their arrays
+// since the last reset (first: the first offending element offset, -1 if
+// none); -3 in the product build, -4 on a CUDA error.
+int bounds_violations(int reset, long long *first);
 inline int remap_tiles(int ox, int oy) { return ((ox + 31) / 32) * ((oy + 7) / 8); }
 
 // FP16 scales (device floats sc[]) from exact energy bounds (max |.| <= the

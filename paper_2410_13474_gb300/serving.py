@@ -69,16 +69,23 @@ class Scheduler:
     if the sum over slots stays within the budget.  A request whose workspace
     alone exceeds the budget is rejected (status ENOMEM).
     slots: concurrent batches (one stream each); max_batch: views per batch.
+    overlap_bytes: latency guard for concurrent batches, with workspace bytes
+    as the measure of a batch's work.  While a batch above overlap_bytes runs,
+    another slot starts only a batch of at most overlap_bytes (small views
+    pass a large one instead of queueing behind it, but two large ones never
+    share the GPU, which would stretch both); None lets any batches overlap.
     """
 
     def __init__(self, executor, budget_bytes: int, slots: int = 2, max_batch: int = 16,
-                 clock=time.perf_counter, idle_sleep: float = 2e-4):
+                 clock=time.perf_counter, idle_sleep: float = 2e-4,
+                 overlap_bytes: int | None = None):
         self.ex = executor
         self.budget = int(budget_bytes)
         self.slots = int(slots)
         self.max_batch = int(max_batch)
         self.clock = clock
         self.idle_sleep = idle_sleep
+        self.overlap_bytes = None if overlap_bytes is None else int(overlap_bytes)
 
     def run(self, requests) -> Stats:
         reqs = sorted(requests, key=lambda r: r.t_arrival)
@@ -117,6 +124,9 @@ class Scheduler:
                 if s in inflight or not pending:
                     continue
                 room = self.budget - sum(reserved[k] for k in range(self.slots) if k != s)
+                if (self.overlap_bytes is not None and inflight
+                        and max(b[2] for b in inflight.values()) > self.overlap_bytes):
+                    room = min(room, self.overlap_bytes)
                 batch, nbytes = [], 0
                 while pending and len(batch) < self.max_batch:
                     r = pending[0]

@@ -63,3 +63,24 @@ def test_latency_percentiles():
     sched = Scheduler(ex, budget_bytes=2**30, slots=1, max_batch=1, clock=ex.clock)
     st = sched.run([Request(i, 0, None, 0.0, ws_bytes=1) for i in range(4)])
     assert abs(st.p99_ms - 19.85) < 0.2 and abs(st.wall_s - 0.02) < 1e-9
+
+
+def test_overlap_guard_keeps_large_batches_apart():
+    """With overlap_bytes set, two batches above it never run at once, and a
+    small batch may start beside a large one."""
+    big, small = 8 * 2**20, 2**20
+    ex = SimExecutor(fixed=1e-3, per_byte=1e-9)
+    sched = Scheduler(ex, budget_bytes=2**30, slots=2, max_batch=1, clock=ex.clock,
+                      overlap_bytes=4 * 2**20)
+    reqs = _reqs(200, 400.0, [big, small, big, small, small])
+    st = sched.run(reqs)
+    assert st.completed == 200
+    size = {r.rid: r.ws_bytes for r in reqs}
+    spans = [(t, e, sum(size[i] for i in rids)) for (_, rids, t), e in zip(ex.launched, ex.ends)]
+    overlapped_small = 0
+    for k, (t0, e0, b0) in enumerate(spans):
+        for t1, e1, b1 in spans[k + 1:]:
+            if t1 < e0 and t0 < e1:          # the two batches overlap in time
+                assert not (b0 > 4 * 2**20 and b1 > 4 * 2**20)
+                overlapped_small += 1
+    assert overlapped_small > 0
