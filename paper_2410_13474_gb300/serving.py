@@ -69,6 +69,11 @@ class Scheduler:
     if the sum over slots stays within the budget.  A request whose workspace
     alone exceeds the budget is rejected (status ENOMEM).
     slots: concurrent batches (one stream each); max_batch: views per batch.
+    batch_queue: adaptive batching.  A batch takes every queued request (up to
+    max_batch) only while at least batch_queue requests wait; with fewer it
+    takes the oldest one alone.  A batch's requests all complete when the
+    batch does, so batching a short queue delays its first requests without
+    a throughput gain; a long queue (a backlog) is where batching pays.
     overlap_bytes: latency guard for concurrent batches, with workspace bytes
     as the measure of a batch's work.  While a batch above overlap_bytes runs,
     another slot starts only a batch of at most overlap_bytes (small views
@@ -78,7 +83,7 @@ class Scheduler:
 
     def __init__(self, executor, budget_bytes: int, slots: int = 2, max_batch: int = 16,
                  clock=time.perf_counter, idle_sleep: float = 2e-4,
-                 overlap_bytes: int | None = None):
+                 overlap_bytes: int | None = None, batch_queue: int = 1):
         self.ex = executor
         self.budget = int(budget_bytes)
         self.slots = int(slots)
@@ -86,6 +91,7 @@ class Scheduler:
         self.clock = clock
         self.idle_sleep = idle_sleep
         self.overlap_bytes = None if overlap_bytes is None else int(overlap_bytes)
+        self.batch_queue = max(1, int(batch_queue))
 
     def run(self, requests) -> Stats:
         reqs = sorted(requests, key=lambda r: r.t_arrival)
@@ -128,7 +134,8 @@ class Scheduler:
                         and max(b[2] for b in inflight.values()) > self.overlap_bytes):
                     room = min(room, self.overlap_bytes)
                 batch, nbytes = [], 0
-                while pending and len(batch) < self.max_batch:
+                limit = self.max_batch if len(pending) >= self.batch_queue else 1
+                while pending and len(batch) < limit:
                     r = pending[0]
                     if nbytes + r.ws_bytes > room:
                         break

@@ -84,3 +84,17 @@ def test_overlap_guard_keeps_large_batches_apart():
                 assert not (b0 > 4 * 2**20 and b1 > 4 * 2**20)
                 overlapped_small += 1
     assert overlapped_small > 0
+
+
+def test_adaptive_batching_only_batches_a_backlog():
+    """batch_queue = 4: batches of more than one request start only from a
+    queue of at least four; under light load every request runs alone."""
+    ex = SimExecutor(fixed=1e-3)
+    sched = Scheduler(ex, budget_bytes=2**30, slots=1, max_batch=16, clock=ex.clock, batch_queue=4)
+    st = sched.run(_reqs(200, 50.0, [2**20]))     # 50/s on a 1 ms device: no queue
+    assert st.completed == 200 and st.mean_batch == 1.0
+    ex = SimExecutor(fixed=20e-3)
+    sched = Scheduler(ex, budget_bytes=2**30, slots=1, max_batch=16, clock=ex.clock, batch_queue=4)
+    st = sched.run(_reqs(200, 1000.0, [2**20]))   # 1000/s on a 20 ms device: a backlog
+    assert st.completed == 200 and st.mean_batch > 4
+    assert all(len(rids) == 1 or len(rids) >= 4 for _, rids, _ in ex.launched)

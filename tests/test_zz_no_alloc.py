@@ -81,3 +81,38 @@ def test_noalloc_rejects_sizes_beyond_its_maximum(nf):
     H = torch.zeros((256, 256), dtype=torch.complex64, device="cuda")
     rc, _ = _noalloc(nf, H, 532e-9, 0.4e-6, nf.View(z=1e-3))
     assert rc == nf.EUNSUPPORTED
+
+
+def test_noalloc_allocates_no_device_memory(nf):
+    """Repeated calls leave the device's free memory unchanged (cudaMemGetInfo):
+    the library allocates nothing on this path.  Outputs are allocated up
+    front, and one warm-up round loads the kernels' code first (lazy module
+    loading takes device memory on a kernel's first launch)."""
+    jobs = []
+    for k, (ny, nx, lam, pitch, kw) in enumerate(CASES):
+        rng = np.random.default_rng(100 + k)
+        H = torch.from_numpy((rng.standard_normal((ny, nx)) +
+                              1j * rng.standard_normal((ny, nx))).astype(np.complex64)).cuda()
+        for kind in (nf.OUT_FIELD, nf.OUT_INTENSITY):
+            view = nf.View(kind=kind, **kw)
+            info = nf.view_plan(lam, pitch, nx, ny, view)
+            dt = torch.float32 if kind == nf.OUT_INTENSITY else torch.complex64
+            out = torch.empty((info["out_ny"], info["out_nx"]), dtype=dt, device="cuda")
+            jobs.append((nf._Params(lam, pitch, nx, ny, nf.FP32, 0, 0), view._c(), H, out))
+    st = torch.cuda.current_stream()
+
+    def run_all():
+        for prm, v, H, out in jobs:
+            rc = nf.lib().nufds_reconstruct_noalloc(ctypes.byref(prm), ctypes.byref(v),
+                                                    ctypes.c_void_p(H.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr()),
+                                                    ctypes.c_void_p(st.cuda_stream))
+            assert rc == nf.OK, nf.status_string(rc)
+        torch.cuda.synchronize()
+
+    run_all()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        run_all()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
