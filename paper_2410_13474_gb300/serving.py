@@ -36,7 +36,8 @@ class Request:
 @dataclass
 class Stats:
     n: int
-    completed: int
+    completed: int                 # finished with status 0
+    failed: int                    # finished with an error status (not in throughput or latency)
     rejected: int
     wall_s: float
     throughput: float              # completed views per second of wall time
@@ -99,7 +100,7 @@ class Scheduler:
         inflight = {}                      # slot -> (batch, handle, bytes)
         reserved = [0] * self.slots        # retained workspace per slot (high-water mark)
         inflight_bytes = max_inflight = 0
-        nxt = done = rejected = 0
+        nxt = done = rejected = failed = 0
         n = len(reqs)
         batch_sizes = []
         t0 = self.clock()
@@ -122,6 +123,7 @@ class Scheduler:
                     for r, st in zip(batch, statuses):
                         r.t_done = t
                         r.status = st
+                        failed += st != 0
                     done += len(batch)
                     inflight_bytes -= nbytes
                     del inflight[s]
@@ -153,11 +155,20 @@ class Scheduler:
                 batch_sizes.append(len(batch))
                 progressed = True
             if not progressed:
-                self.ex.idle(t0 + reqs[nxt].t_arrival if nxt < n else None, self.idle_sleep)
+                # nothing to do until an arrival or a completion: with every
+                # slot busy the executor may block on a running batch (one
+                # slot: no arrival can start before it ends); with none busy,
+                # sleep to the next arrival
+                handles = [b[1] for b in inflight.values()]
+                self.ex.idle(t0 + reqs[nxt].t_arrival if nxt < n else None, self.idle_sleep,
+                             wait=handles[0] if self.slots == 1 and handles else None,
+                             busy=bool(handles))
         wall = self.clock() - t0
-        lat = [1e3 * (r.t_done - r.t_arrival) for r in reqs if r.t_done is not None]
-        return Stats(n=n, completed=done, rejected=rejected, wall_s=wall,
-                     throughput=done / wall if wall > 0 else float("nan"),
+        lat = [1e3 * (r.t_done - r.t_arrival) for r in reqs
+               if r.t_done is not None and r.status == 0]
+        ok = done - failed
+        return Stats(n=n, completed=ok, failed=failed, rejected=rejected, wall_s=wall,
+                     throughput=ok / wall if wall > 0 else float("nan"),
                      p50_ms=percentile(lat, 0.50), p99_ms=percentile(lat, 0.99),
                      mean_batch=(sum(batch_sizes) / len(batch_sizes)) if batch_sizes else 0.0,
                      batches=len(batch_sizes), max_inflight_bytes=max_inflight)
@@ -216,8 +227,23 @@ class GpuExecutor:
     def statuses(self, handle):
         return handle[1]
 
-    def idle(self, next_arrival, sleep):
-        time.sleep(sleep)
+    def idle(self, next_arrival, sleep, wait=None, busy=True):
+        """Pass the time until something can happen: block on `wait` (a
+        running batch) when given; with nothing running, sleep until the next
+        arrival (the last 0.2 ms by polling the clock, since a sleep can
+        overrun by tens of microseconds); otherwise sleep `sleep` seconds."""
+        if wait is not None:
+            wait[0].synchronize()
+            return
+        if not busy and next_arrival is not None:
+            while True:
+                left = next_arrival - time.perf_counter()
+                if left <= 0:
+                    return
+                if left > 2e-4:
+                    time.sleep(left - 2e-4)
+        else:
+            time.sleep(sleep)
 
 
 class SimExecutor:
@@ -246,7 +272,7 @@ class SimExecutor:
     def statuses(self, handle):
         return handle[1]
 
-    def idle(self, next_arrival, sleep):
+    def idle(self, next_arrival, sleep, wait=None, busy=True):
         cands = [e for e in self.ends if e > self.t]
         if next_arrival is not None and next_arrival > self.t:
             cands.append(next_arrival)

@@ -98,3 +98,19 @@ def test_adaptive_batching_only_batches_a_backlog():
     st = sched.run(_reqs(200, 1000.0, [2**20]))   # 1000/s on a 20 ms device: a backlog
     assert st.completed == 200 and st.mean_batch > 4
     assert all(len(rids) == 1 or len(rids) >= 4 for _, rids, _ in ex.launched)
+
+
+def test_failed_requests_are_not_counted_as_served():
+    """A request whose batch returns an error status counts as failed: it is
+    left out of the completed count, the throughput and the latencies."""
+    class Failing(SimExecutor):
+        def launch(self, slot, batch):
+            end, st = super().launch(slot, batch)
+            return (end, [-2 if r.rid % 4 == 0 else 0 for r in batch])
+
+    ex = Failing(fixed=1e-3)
+    sched = Scheduler(ex, budget_bytes=2**30, slots=1, max_batch=1, clock=ex.clock)
+    reqs = _reqs(100, 100.0, [2**20])
+    st = sched.run(reqs)
+    assert st.failed == 25 and st.completed == 75
+    assert abs(st.throughput - 75 / st.wall_s) < 1e-9
