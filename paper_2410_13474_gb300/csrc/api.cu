@@ -838,9 +838,68 @@ struct BatchWs {
     };
     std::list<Graph> graphs;
     cudaStream_t cap = nullptr;  // private stream the graphs are captured on
+    cudaEvent_t last = nullptr;  // recorded after the last wave that used this workspace
+    uint64_t used = 0;           // recency, for eviction
+    int busy = 0;                // host threads inside run_wave with it
 };
 static std::mutex g_batch_mu;
 static std::map<std::pair<int, cudaStream_t>, BatchWs *> g_batch;  // per (device, stream)
+static uint64_t g_batch_clock = 0;
+// Batch workspaces kept per device.  A caller that runs batches on ever new
+// streams would otherwise keep one workspace per stream it ever used (up to
+// the batch cap each); the least recently used idle one is freed instead.
+constexpr int kMaxBatchWs = 4;
+
+static void batch_ws_free(BatchWs *B) {
+    if (B->last) cudaEventSynchronize(B->last);
+    for (auto &g : B->graphs) cudaGraphExecDestroy(g.exec);
+    cudaFree(B->dev);
+    for (int i = 0; i < BatchWs::kRing; ++i) {
+        if (B->host_ev[i]) {
+            cudaEventSynchronize(B->host_ev[i]);
+            cudaEventDestroy(B->host_ev[i]);
+        }
+        cudaFreeHost(B->host[i]);
+    }
+    if (B->cap) cudaStreamDestroy(B->cap);
+    if (B->last) cudaEventDestroy(B->last);
+    delete B;
+}
+
+// The workspace of (dev, st), marked busy until release; evicts the least
+// recently used idle workspace of the device beyond kMaxBatchWs.
+static BatchWs *batch_ws_acquire(int dev, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    const auto key = std::make_pair(dev, st);
+    auto it = g_batch.find(key);
+    if (it == g_batch.end()) {
+        for (;;) {
+            int count = 0;
+            auto lru = g_batch.end();
+            for (auto jt = g_batch.begin(); jt != g_batch.end(); ++jt) {
+                if (jt->first.first != dev) continue;
+                ++count;
+                if (!jt->second->busy && (lru == g_batch.end() || jt->second->used < lru->second->used))
+                    lru = jt;
+            }
+            if (count < kMaxBatchWs || lru == g_batch.end()) break;
+            batch_ws_free(lru->second);
+            g_batch.erase(lru);
+        }
+        it = g_batch.emplace(key, new BatchWs()).first;
+    }
+    BatchWs *B = it->second;
+    B->used = ++g_batch_clock;
+    B->busy++;
+    return B;
+}
+struct BatchWsHold {
+    BatchWs *B;
+    ~BatchWsHold() {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        B->busy--;
+    }
+};
 
 static size_t batch_cap_bytes() {
     const char *e = getenv("NUFDS_BATCH_WS_GB");
@@ -954,13 +1013,12 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
     const size_t need = views_bytes + scr_bytes + desc_bytes;
     int dev;
     cudaGetDevice(&dev);
-    BatchWs *B;
-    {
-        std::lock_guard<std::mutex> lk(g_batch_mu);
-        BatchWs *&slot_ws = g_batch[std::make_pair(dev, st)];
-        if (!slot_ws) slot_ws = new BatchWs();
-        B = slot_ws;
-    }
+    BatchWs *B = batch_ws_acquire(dev, st);
+    BatchWsHold hold{B};
+    // a stream handle can be reused after its stream was destroyed: order
+    // after the last wave that used this workspace
+    if (B->last && cudaStreamWaitEvent(st, B->last, 0) != cudaSuccess)
+        return CUDA_FAIL("cudaStreamWaitEvent");
     if (need > B->bytes) {
         cudaStreamSynchronize(st);
         for (auto &g : B->graphs) cudaGraphExecDestroy(g.exec);
@@ -1260,9 +1318,11 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
                 rc = NUFDS_ECUDA;
         }
         const char *where = "tables";
-        if (!rc && (where = "stretch"))
+        if (!rc) {
+            where = "stretch";
             rc = launch_stretch_batch((const StretchArgs *)(ddesc + o_sa),
                                       (const int *)(ddesc + o_soff), n, tst, prec, st);
+        }
         for (int i = 0; i < n && !rc && prec == NUFDS_FP16_STORE; ++i) {
             const BandWork &bw = bws[i];
             rc = launch_energy((const char *)R[i].Bf + eb * (size_t)bw.bx0 * w[i].V.npy,
@@ -1283,14 +1343,24 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
             }
             return r;
         };
-        if (!rc && (where = "rows_y")) rc = rows_pass(0);
-        if (!rc && (where = "transpose"))
+        if (!rc) {
+            where = "rows_y";
+            rc = rows_pass(0);
+        }
+        if (!rc) {
+            where = "transpose";
             rc = launch_transpose_batch((const TrItem *)(ddesc + o_tr),
                                         (const int *)(ddesc + o_toff), ntr, ttr, prec, st);
-        if (!rc && (where = "rows_x")) rc = rows_pass(1);
-        if (!rc && (where = "remap"))
+        }
+        if (!rc) {
+            where = "rows_x";
+            rc = rows_pass(1);
+        }
+        if (!rc) {
+            where = "remap";
             rc = launch_remap_batch((const RemapArgs *)(ddesc + o_ra),
                                     (const int *)(ddesc + o_roff2), n, trm, prec, st);
+        }
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
         if (rc || ce != cudaSuccess) {
             if (ce == cudaSuccess) cudaGraphDestroy(graph);
@@ -1312,6 +1382,9 @@ static int run_wave(std::vector<BatchView> &w, int prec, cudaStream_t st, int32_
     }
     if (cudaGraphLaunch(exec, st) != cudaSuccess) return CUDA_FAIL("cudaGraphLaunch");
     count_launch();
+    if ((!B->last && cudaEventCreateWithFlags(&B->last, cudaEventDisableTiming) != cudaSuccess) ||
+        cudaEventRecord(B->last, st) != cudaSuccess)
+        return CUDA_FAIL("cudaEventRecord");
     for (auto &b : w)
         if (statuses) statuses[b.idx] = NUFDS_OK;
     return NUFDS_OK;

@@ -6,8 +6,9 @@
 //   lambda f_y' = (1 - u^2)^(1/4) g(v / sqrt(1 - u^2)),
 // where g(s) = s 2F1(1/2, 3/4; 3/2; s^2) = int_0^s (1 - t^2)^(-3/4) dt
 // (integrating Eq. 15 in f_x).  g is evaluated from two series of that
-// integral: the binomial series of the integrand around t = 0 for |s| <= 3/4,
-// and around t = 1 (in powers of 1 - s) above, with g(1) = B(1/2, 1/4) / 2.
+// integral: the binomial series of the integrand around t = 0 for |s| <= 1/2,
+// and around t = 1 (in powers of 1 - s) above, with g(1) = B(1/2, 1/4) / 2;
+// either needs at most ~30 terms for 1e-18.
 //
 // Every value that sets a sampling position is computed here in FP64, once
 // per plan (or per off-lattice view), and stored as an integer base on the
@@ -17,38 +18,74 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "internal.cuh"
 
 namespace nufds {
 
+// Coefficients of the two series, c_n = (3/4)_n / n! by its recurrence in FP64:
+// a_n = c_n / (2n + 1) (about t = 0) and b_n = c_n / (n + 1/4) (about t = 1),
+// tabulated once so the series loops carry no FP64 division (slow on this GPU).
+constexpr int kGTerms = 200;
+struct GCoef {
+    double a[kGTerms], b[kGTerms];
+};
+static GCoef make_gcoef() {
+    GCoef t;
+    double c = 1.0;
+    for (int n = 0; n < kGTerms; ++n) {
+        if (n > 0) c *= (n - 0.25) / n;
+        t.a[n] = c / (2.0 * n + 1.0);
+        t.b[n] = c / (n + 0.25);
+    }
+    return t;
+}
+static const GCoef h_gcoef = make_gcoef();
+__constant__ GCoef c_gcoef;
+
+static int gcoef_init() {
+    static std::mutex mu;
+    static std::map<int, bool> ready;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -4;
+    std::lock_guard<std::mutex> lk(mu);
+    if (ready[dev]) return 0;
+    if (cudaMemcpyToSymbol(c_gcoef, &h_gcoef, sizeof(GCoef)) != cudaSuccess) return -4;
+    ready[dev] = true;
+    return 0;
+}
+
 __host__ __device__ inline double g_series(double s, double g1) {
+#ifdef __CUDA_ARCH__
+    const GCoef &k = c_gcoef;
+#else
+    const GCoef &k = h_gcoef;
+#endif
     double a = fabs(s);
     double r;
-    if (a <= 0.75) {
-        // sum_n c_n s^(2n+1) / (2n+1), c_n = (3/4)_n / n!
-        double s2 = a * a, p = a, c = 1.0, sum = a;
-        for (int n = 1; n < 200; ++n) {
-            c *= (n - 0.25) / n;
+    if (a <= 0.5) {
+        // sum_n c_n s^(2n+1) / (2n+1): terms fall by s^2 <= 1/4
+        double s2 = a * a, p = a, sum = a;
+        for (int n = 1; n < kGTerms; ++n) {
             p *= s2;
-            double t = c * p / (2.0 * n + 1.0);
+            double t = k.a[n] * p;
             sum += t;
             if (t < 1e-18 * sum) break;
         }
         r = sum;
     } else {
-        // g(1) - 2^(-3/4) sum_n c_n 2^(-n) e^(n + 1/4) / (n + 1/4), e = 1 - s
+        // g(1) - 2^(-3/4) sum_n c_n 2^(-n) e^(n + 1/4) / (n + 1/4), e = 1 - s:
+        // terms fall by e/2 < 1/4
         double e = 1.0 - a;
         if (e <= 0.0) {
             r = g1;
         } else {
-            double q = sqrt(sqrt(e)), c = 1.0, h = 1.0, sum = 0.0;
-            for (int n = 0; n < 200; ++n) {
-                if (n > 0) {
-                    c *= (n - 0.25) / n;
-                    h *= 0.5 * e;
-                }
-                double t = c * h * q / (n + 0.25);
+            double q = sqrt(sqrt(e)), h = 1.0, sum = 0.0;
+            for (int n = 0; n < kGTerms; ++n) {
+                if (n > 0) h *= 0.5 * e;
+                double t = k.b[n] * h * q;
                 sum += t;
                 if (t < 1e-18 * sum) break;
             }
@@ -76,8 +113,10 @@ __host__ __device__ inline void poly_g(const MapFn &m, double s, double *g, doub
     *gp = p + s * d;
 }
 
+// gs (optional): the two g values of the exact map, g(u / sqrt(ay)) and
+// g(v / sqrt(ax)), which the Jacobian at the same point reuses
 __host__ __device__ inline void phi_uv(double u, double v, double g1, const MapFn &m, double *up,
-                                       double *vp) {
+                                       double *vp, double *gs = nullptr) {
     double ay = 1.0 - v * v, ax = 1.0 - u * u;
     if (m.poly) {
         double gx, gy, d;
@@ -87,8 +126,13 @@ __host__ __device__ inline void phi_uv(double u, double v, double g1, const MapF
         *vp = sqrt(sqrt(ax)) * gy;
         return;
     }
-    *up = sqrt(sqrt(ay)) * g_series(u / sqrt(ay), g1);
-    *vp = sqrt(sqrt(ax)) * g_series(v / sqrt(ax), g1);
+    const double gu = g_series(u / sqrt(ay), g1), gv = g_series(v / sqrt(ax), g1);
+    *up = sqrt(sqrt(ay)) * gu;
+    *vp = sqrt(sqrt(ax)) * gv;
+    if (gs) {
+        gs[0] = gu;
+        gs[1] = gv;
+    }
 }
 
 void host_phi(double u, double v, double *up, double *vp, const MapFn &m) {
@@ -135,7 +179,8 @@ void map_fit_paper_poly(double lam, double pitch, MapFn *m) {
 // Jacobian d(u', v')/d(u, v) of the stretch (Eq. 15 on the diagonal).  For the
 // surrogate: du'/du = ay^(-1/4) g'(s), du'/dv = -v/2 ay^(-3/4) g(s) +
 // u v ay^(-5/4) g'(s), s = u / sqrt(ay) (and x <-> y).
-__device__ inline void jac_uv(double u, double v, double g1, const MapFn &m, double J[4]) {
+__device__ inline void jac_uv(double u, double v, double g1, const MapFn &m, double J[4],
+                              const double *gs = nullptr) {
     double ay = 1.0 - v * v, ax = 1.0 - u * u;
     if (m.poly) {
         double gy, dy, gx, dx;
@@ -151,7 +196,8 @@ __device__ inline void jac_uv(double u, double v, double g1, const MapFn &m, dou
     double r34 = 1.0 / sqrt(sqrt(r * r * r));  // r^(-3/4)
     J[0] = sqrt(ay) * r34;
     J[3] = sqrt(ax) * r34;
-    double gy = g_series(u / sqrt(ay), g1), gx = g_series(v / sqrt(ax), g1);
+    double gy = gs ? gs[0] : g_series(u / sqrt(ay), g1);
+    double gx = gs ? gs[1] : g_series(v / sqrt(ax), g1);
     J[1] = -0.5 * v * gy / sqrt(sqrt(ay * ay * ay)) + u * v * r34 / sqrt(ay);
     J[2] = -0.5 * u * gx / sqrt(sqrt(ax * ax * ax)) + u * v * r34 / sqrt(ax);
 }
@@ -173,12 +219,12 @@ __device__ bool pullback_uv(double up, double vp, double g1, const MapFn &m, dou
         u *= sc;
         v *= sc;
     }
-    double fu, fv;
-    phi_uv(u, v, g1, m, &fu, &fv);
+    double fu, fv, gs[2] = {0.0, 0.0};  // gs: the g values at (u, v), for the Jacobian
+    phi_uv(u, v, g1, m, &fu, &fv, gs);
     double res = fabs(fu - up) + fabs(fv - vp);
     for (int it = 0; it < 100; ++it) {
         double J[4];
-        jac_uv(u, v, g1, m, J);
+        jac_uv(u, v, g1, m, J, gs);
         double det = J[0] * J[3] - J[1] * J[2];
         double ru = up - fu, rv = vp - fv;
         double du = (J[3] * ru - J[1] * rv) / det;
@@ -188,14 +234,16 @@ __device__ bool pullback_uv(double up, double vp, double g1, const MapFn &m, dou
         for (int h = 0; h < 60; ++h) {
             double un = u + step * du, vn = v + step * dv;
             if (un * un + vn * vn < 1.0) {
-                double gu, gv;
-                phi_uv(un, vn, g1, m, &gu, &gv);
+                double gu, gv, gsn[2] = {0.0, 0.0};
+                phi_uv(un, vn, g1, m, &gu, &gv, gsn);
                 double rn = fabs(gu - up) + fabs(gv - vp);
                 if (rn < res || rn == 0.0 || step * (fabs(du) + fabs(dv)) <= tol) {
                     u = un;
                     v = vn;
                     fu = gu;
                     fv = gv;
+                    gs[0] = gsn[0];
+                    gs[1] = gsn[1];
                     res = rn;
                     ok = true;
                     break;
@@ -388,6 +436,7 @@ int launch_pullback_table(double lam, double pitch, int nx, int ny, long kx0, in
                           double2 *coarse) {
     long n = (long)nkx * nky;
     if (n <= 0) return 0;
+    if (gcoef_init()) return -4;
     const int step = kPullbackStep;
     const int ncx = (nkx - 1 + step - 1) / step + 1, ncy = (nky - 1 + step - 1) / step + 1;
     if (coarse && (ncx < 2 || ncy < 2)) coarse = nullptr;
@@ -409,6 +458,7 @@ int launch_remap_table(double lam, double pitch, int nx, int ny, double z, doubl
                        cudaStream_t st, int plain, const MapFn &m) {
     long n = (long)ox * oy;
     if (n <= 0) return 0;
+    if (gcoef_init()) return -4;
     k_remap_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(lam, pitch, nx, ny, z, cx, cy, px,
                                                               py, ox, oy, g_at_one(), m, base, frac, plain);
     count_launch();

@@ -123,3 +123,35 @@ def test_batch_views_match_oracle(nf):
     print("batch vs oracle: worst rel_l2 %.3e over %d views" % (worst, len(outs)))
     for p in {id(p): p for p in plans}.values():
         p.close()
+
+
+def test_batches_on_many_streams_keep_a_bounded_workspace(nf):
+    """Batches on ten successive new streams: the results stay bitwise equal,
+    and the device memory held afterwards is bounded by the library's four
+    retained batch workspaces per device, not one per stream ever used."""
+    n, lam, pitch, z = 256, 532e-9, 0.35e-6, 0.8e-3
+    pl = nf.Plan(lam, pitch, n, n, _holo(n, 11))
+    views = _views(nf, pl, z, 11)
+    outs = [pl.output_like(v) for v in views]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    s0 = torch.cuda.Stream()
+    assert all(c == nf.OK for c in nf.reconstruct_batch([pl] * len(views), views, outs, stream=s0))
+    torch.cuda.synchronize()
+    ref = [o.cpu().numpy() for o in outs]
+    per = free0 - torch.cuda.mem_get_info()[0]     # one stream's batch workspace
+    streams = [s0]
+    for _ in range(10):
+        s = torch.cuda.Stream()
+        streams.append(s)
+        for o in outs:
+            o.zero_()
+        torch.cuda.synchronize()
+        assert all(c == nf.OK for c in nf.reconstruct_batch([pl] * len(views), views, outs, stream=s))
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert np.array_equal(o.cpu().numpy(), r)
+    held = free0 - torch.cuda.mem_get_info()[0]
+    print("one workspace %.1f MB, held after 11 streams %.1f MB" % (per / 2**20, held / 2**20))
+    assert per > 0 and held <= 4 * per + (64 << 20), (per, held)
+    pl.close()
