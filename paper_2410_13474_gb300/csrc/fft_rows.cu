@@ -845,6 +845,17 @@ static bool choose_radices(int L, FftPlan &p) {
     int best = kMaxPasses + 1;
     factor_sets(L, cur, sets, best);
     if (sets.empty() || best < 2) return false;
+    // lowest bank-conflict cost; among equal costs the most balanced radices
+    // (smallest sum of squares: fewer values live in registers in the largest
+    // passes), then the smallest first radix.  Measured over every minimum-
+    // pass order of 23040 and 16384, this picks the fastest order of each
+    // (10 x 12 x 12 x 16: view passes 20.54 ms against 21.31 ms for the first
+    // equal-cost order found; 8 x 8 x 16 x 16 for the spectrum passes).
+    auto sq = [](const std::vector<int> &r) {
+        int m = 0;
+        for (int x : r) m += x * x;
+        return m;
+    };
     double bc = 1e30;
     std::vector<int> bo;
     for (auto &m : sets) {
@@ -852,7 +863,11 @@ static bool choose_radices(int L, FftPlan &p) {
         std::sort(perm.begin(), perm.end());
         do {
             double c = order_cost(perm);
-            if (c < bc - 1e-9) {
+            const bool better =
+                c < bc - 1e-9 ||
+                (c < bc + 1e-9 &&
+                 (sq(perm) < sq(bo) || (sq(perm) == sq(bo) && perm[0] < bo[0])));
+            if (better) {
                 bc = c;
                 bo = perm;
             }
