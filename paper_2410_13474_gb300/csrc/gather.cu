@@ -341,7 +341,7 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
     // a warp covers 32 consecutive band points along y (measured faster than
     // 8 x 4 blocks, whose lanes' windows spread over more lines of G)
     const int jy = bx * 32 + threadIdx.x;
-    const int jx = a.jx0 + by * 8 + threadIdx.y;
+    const int jx = a.jx0 + by * kStretchRows + threadIdx.y;
     const bool inside = jx - a.jx0 < (a.jn ? a.jn : a.npx) && jx < a.npx && jy < a.npy;
     const long kx = a.kc_x + jx - a.npx / 2, ky = a.kc_y + jy - a.npy / 2;
     bool valid = false;
@@ -403,7 +403,7 @@ __device__ __forceinline__ void stretch_body(const StretchArgs &a, int bx, int b
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 4) k_stretch(StretchArgs a) {
+__global__ void __launch_bounds__(32 * kStretchRows, 32 / kStretchRows) k_stretch(StretchArgs a) {
     stretch_body<T>(a, blockIdx.x, blockIdx.y);
 }
 
@@ -418,7 +418,7 @@ __device__ __forceinline__ int find_item(const int *off, int nitems, int b) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 4) k_stretch_batch(const StretchArgs *__restrict__ items,
+__global__ void __launch_bounds__(32 * kStretchRows, 32 / kStretchRows) k_stretch_batch(const StretchArgs *__restrict__ items,
                                                        const int *__restrict__ off, int nitems) {
     const int it = find_item(off, nitems, blockIdx.x);
     const StretchArgs &a = items[it];
@@ -434,7 +434,7 @@ __device__ __forceinline__ void remap_body(const RemapArgs &a, int bx, int by) {
     const T *Q = (const T *)a.Q;
     const float qinv = a.sc_q ? 1.0f / *a.sc_q : 1.0f;
     const int i = bx * 32 + threadIdx.x;
-    const int j = by * 8 + threadIdx.y;
+    const int j = by * kRemapRows + threadIdx.y;
     const bool valid = i < a.ox && j < a.oy;
     int2 b = make_int2(0, 0);
     uint2 F = make_uint2(0u, 0u);
@@ -591,12 +591,12 @@ __global__ void __launch_bounds__(256) k_remap_linear(RemapArgs a) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 4) k_remap(RemapArgs a) {
+__global__ void __launch_bounds__(32 * kRemapRows, 32 / kRemapRows) k_remap(RemapArgs a) {
     remap_body<T>(a, blockIdx.x, blockIdx.y);
 }
 
 template <class T>
-__global__ void __launch_bounds__(256, 4) k_remap_batch(const RemapArgs *__restrict__ items,
+__global__ void __launch_bounds__(32 * kRemapRows, 32 / kRemapRows) k_remap_batch(const RemapArgs *__restrict__ items,
                                                      const int *__restrict__ off, int nitems) {
     const int it = find_item(off, nitems, blockIdx.x);
     const RemapArgs &a = items[it];
@@ -606,12 +606,15 @@ __global__ void __launch_bounds__(256, 4) k_remap_batch(const RemapArgs *__restr
 
 int launch_stretch(const StretchArgs &a, cudaStream_t st) {
     if (es_init()) return -4;
-    dim3 grid((a.npy + 31) / 32, ((a.jn ? a.jn : a.npx) + 7) / 8);
+    const int rows = a.jn ? a.jn : a.npx;
+    const dim3 grid((a.npy + 31) / 32, (rows + kStretchRows - 1) / kStretchRows),
+        blk(32, kStretchRows);
     if (a.linear && a.prec != PREC_F32) return -3;
-    if (a.linear) k_stretch_linear<<<grid, dim3(32, 8), 0, st>>>(a);
-    else if (a.prec == PREC_F32) k_stretch<float2><<<grid, dim3(32, 8), 0, st>>>(a);
-    else if (a.prec == PREC_F16) k_stretch<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
-    else k_stretch<__nv_bfloat162><<<grid, dim3(32, 8), 0, st>>>(a);
+    if (a.linear)
+        k_stretch_linear<<<dim3((a.npy + 31) / 32, (rows + 7) / 8), dim3(32, 8), 0, st>>>(a);
+    else if (a.prec == PREC_F32) k_stretch<float2><<<grid, blk, 0, st>>>(a);
+    else if (a.prec == PREC_F16) k_stretch<__half2><<<grid, blk, 0, st>>>(a);
+    else k_stretch<__nv_bfloat162><<<grid, blk, 0, st>>>(a);
     count_launch();
     return check_launch();
 }
@@ -620,9 +623,9 @@ int launch_stretch_batch(const StretchArgs *d_items, const int *d_off, int nitem
                          int prec, cudaStream_t st) {
     if (es_init()) return -4;
     if (total <= 0) return 0;
-    if (prec == PREC_F32) k_stretch_batch<float2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
-    else if (prec == PREC_F16) k_stretch_batch<__half2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
-    else k_stretch_batch<__nv_bfloat162><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
+    if (prec == PREC_F32) k_stretch_batch<float2><<<total, dim3(32, kStretchRows), 0, st>>>(d_items, d_off, nitems);
+    else if (prec == PREC_F16) k_stretch_batch<__half2><<<total, dim3(32, kStretchRows), 0, st>>>(d_items, d_off, nitems);
+    else k_stretch_batch<__nv_bfloat162><<<total, dim3(32, kStretchRows), 0, st>>>(d_items, d_off, nitems);
     count_launch();
     return check_launch();
 }
@@ -631,21 +634,22 @@ int launch_remap_batch(const RemapArgs *d_items, const int *d_off, int nitems, i
                        cudaStream_t st) {
     if (es_init()) return -4;
     if (total <= 0) return 0;
-    if (prec == PREC_F32) k_remap_batch<float2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
-    else if (prec == PREC_F16) k_remap_batch<__half2><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
-    else k_remap_batch<__nv_bfloat162><<<total, dim3(32, 8), 0, st>>>(d_items, d_off, nitems);
+    if (prec == PREC_F32) k_remap_batch<float2><<<total, dim3(32, kRemapRows), 0, st>>>(d_items, d_off, nitems);
+    else if (prec == PREC_F16) k_remap_batch<__half2><<<total, dim3(32, kRemapRows), 0, st>>>(d_items, d_off, nitems);
+    else k_remap_batch<__nv_bfloat162><<<total, dim3(32, kRemapRows), 0, st>>>(d_items, d_off, nitems);
     count_launch();
     return check_launch();
 }
 
 int launch_remap(const RemapArgs &a, cudaStream_t st) {
     if (es_init()) return -4;
-    dim3 grid((a.ox + 31) / 32, (a.oy + 7) / 8);
+    const dim3 grid((a.ox + 31) / 32, (a.oy + kRemapRows - 1) / kRemapRows), blk(32, kRemapRows);
     if (a.linear && a.prec != PREC_F32) return -3;
-    if (a.linear) k_remap_linear<<<grid, dim3(32, 8), 0, st>>>(a);
-    else if (a.prec == PREC_F32) k_remap<float2><<<grid, dim3(32, 8), 0, st>>>(a);
-    else if (a.prec == PREC_F16) k_remap<__half2><<<grid, dim3(32, 8), 0, st>>>(a);
-    else k_remap<__nv_bfloat162><<<grid, dim3(32, 8), 0, st>>>(a);
+    if (a.linear)
+        k_remap_linear<<<dim3((a.ox + 31) / 32, (a.oy + 7) / 8), dim3(32, 8), 0, st>>>(a);
+    else if (a.prec == PREC_F32) k_remap<float2><<<grid, blk, 0, st>>>(a);
+    else if (a.prec == PREC_F16) k_remap<__half2><<<grid, blk, 0, st>>>(a);
+    else k_remap<__nv_bfloat162><<<grid, blk, 0, st>>>(a);
     count_launch();
     return check_launch();
 }
