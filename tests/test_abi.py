@@ -173,3 +173,11 @@ def test_planner_limits(built):
     one = nf.view_plan(lam, pitch, 256, 256, nf.View(z=0.5, width=1e-5, height=1e-5, out_nx=1,
                                                     out_ny=1))
     assert one["out_nx"] == 1 and one["k_hi_x"] - one["k_lo_x"] <= 2
+
+
+def test_product_library_has_no_bounds_checks(built):
+    """The product build compiles the gathers' bounds checks out: the debug
+    query answers EUNSUPPORTED (no CUDA call is made to say so)."""
+    with pytest.raises(nf.NufdsError) as e:
+        nf.bounds_violations()
+    assert e.value.code == nf.EUNSUPPORTED
